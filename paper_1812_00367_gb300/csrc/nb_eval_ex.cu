@@ -1,0 +1,22 @@
+// nb_eval_ex.cu -- EX instantiations of the evaluation kernel (nb_eval.cuh).
+#include "nb_eval.cuh"
+
+namespace nb {
+
+cudaError_t launch_eval_ex(const Dev &d, int mode, const EvalLaunch &L, int grid,
+                             cudaStream_t st) {
+    switch (mode) {
+    case kModeOut: return launch_eval_t<NB_EX, kModeOut>(d, L, grid, st);
+    case kModeStep: return launch_eval_t<NB_EX, kModeStep>(d, L, grid, st);
+    case kModeInit1: return launch_eval_t<NB_EX, kModeInit1>(d, L, grid, st);
+    case kModeInit2: return launch_eval_t<NB_EX, kModeInit2>(d, L, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int occupancy_ex(int mode) {
+    (void)mode;
+    return occupancy_t<NB_EX, kModeStep>();
+}
+
+}  // namespace nb

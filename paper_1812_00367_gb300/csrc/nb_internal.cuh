@@ -1,0 +1,303 @@
+// nb_internal.cuh -- device-side data structures and primitives of libnb.
+//
+// Everything here is internal to the CUDA library; the public boundary is
+// include/nb.h.  Sm_103a only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/nb.h"
+
+namespace nb {
+
+// ---------------------------------------------------------------- constants
+constexpr int kTPB = 128;      // threads per evaluation CTA (4 warps)
+constexpr int kTJ = 64;        // j-particles per shared-memory tile
+constexpr int kStages = 4;     // TMA pipeline depth
+constexpr int kChunk = 2048;   // particles per select / predict chunk
+constexpr int kSelTPB = 256;   // threads per select / predict CTA
+constexpr int kPlanTPB = 1024; // threads of the single planning CTA
+constexpr int kBuckets = 32;   // active-set size buckets (floor log2 A)
+constexpr int kFp32FlushTiles = 32;  // FP32 path: j-tiles summed in FP32 before
+                                     // promotion to FP64 (32 x 64 = 2048 j)
+
+// device error word bits
+constexpr uint32_t kErrNonFinite = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrIndex = 4u;   // a caller-given index outside its cluster
+
+// wait budget of a bounded device-side wait, nanoseconds
+constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
+
+// ------------------------------------------------------------ packed j-data
+// FP64: x, y, z, m, vx, vy, vz, ax, ay, az as five 16-byte pairs.
+struct alignas(16) J64 {
+    double2 q[5];  // (x,y) (z,m) (vx,vy) (vz,ax) (ay,az)
+};
+// EX: hi/lo single pairs: (xh,yh,zh,mh) (xl,yl,zl,ml) (vxh,vyh,vzh,axh)
+//     (vxl,vyl,vzl,axl) (ayh,azh,ayl,azl)
+struct alignas(16) JEX {
+    float4 q[5];
+};
+// FP32: (xh,yh,zh,m) (xl,yl,zl,ax) (vxh,vyh,vzh,ay) (vxl,vyl,vzl,az)
+struct alignas(16) J32 {
+    float4 q[4];
+};
+
+// ------------------------------------------------------------ planning data
+struct ClusterPlan {
+    int32_t gl;     // lanes cooperating on one i (1..32, power of two)
+    int32_t split;  // number of j-ranges (S)
+    int32_t tiles;  // i-tiles of kTPB / gl active particles
+    int32_t active; // A for this step (0: idle)
+    int64_t item0;  // first work item of the cluster
+    int64_t tile0;  // first i-tile of the cluster (counter index)
+    int64_t pslot0; // first partial-sum slot (only clusters with split > 1 use slots)
+};
+
+struct PlanEntry {  // per active-set bucket
+    int32_t gl;
+    int32_t target_items;  // desired work items per evaluation
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+    int64_t n;
+    int32_t n_clusters;
+    int32_t n_chunks;
+    int32_t precision;
+    int32_t grid_eval;  // persistent evaluation grid (CTAs)
+    const int64_t *offsets;      // [nc+1] particle offsets
+    const int64_t *jofs;         // [nc+1] padded j-array offsets
+    const int32_t *chunk_cluster;// [n_chunks]
+    const int64_t *chunk_begin;  // [n_chunks]
+    const int64_t *chunk_end;    // [n_chunks]
+    const int32_t *cluster_chunk0;  // [nc+1]
+    // state (caller-owned), SoA [3][n]
+    double *m, *x, *v, *a, *j, *s, *c, *t, *dt, *pot;
+    // predicted j-arrays
+    void *jarr;        // precision-specific (J64 / JEX / J32)
+    J64 *jarr64;       // FP64 copy (energy, nb_predict output); == jarr for FP64
+    // select
+    double *chunk_min;
+    int32_t *chunk_cnt;
+    double *tnext;     // [nc]
+    int32_t *nact;     // [nc]
+    int32_t *active;   // [n], cluster c's list at offsets[c]
+    // plan
+    ClusterPlan *plan; // [nc]
+    int64_t *n_items;  // [1]
+    const PlanEntry *table;  // [kBuckets]
+    // reduction scratch
+    double *partial;   // [max_items][10][kTPB]
+    int64_t partial_items;   // capacity in items
+    int32_t *tile_cnt; // [max_tiles]
+    // counters / flags
+    unsigned long long *ctr_steps;
+    double *ctr_inter;
+    unsigned long long *ctr_underflow;
+    uint32_t *err;
+    int32_t *busy;     // [1]: clusters active in the last select
+    double *t_end;     // [1]: clusters whose next block time exceeds it stay idle
+    double *pot_tmp;   // [n] energy potential
+    double *energy_part;  // [blocks][8]
+    // parameters
+    double eps2, eta, eta_init, dt_min, dt_max;
+};
+
+// How one evaluation launch obtains its work.
+struct EvalLaunch {
+    int32_t direct;     // 1: single cluster, host-given list / plan
+    int32_t cluster;    // direct mode
+    int32_t n_active;   // direct mode
+    int32_t gl;         // direct mode
+    int32_t split;      // direct mode
+    int32_t tiles;      // direct mode
+    int32_t identity;   // active list is 0..A-1 of the cluster (init, energy)
+    const int32_t *active;  // direct mode list (global indices)
+    double *out;        // direct mode output [10][n_active]
+    double t_next;      // unused in plan mode (per-cluster tnext)
+};
+
+enum EvalMode { kModeOut = 0, kModeStep = 1, kModeInit1 = 2, kModeInit2 = 3, kModePot = 4 };
+
+// ---------------------------------------------------------- small helpers
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------- FP64 rsqrt
+// 1/sqrt(r2) for r2 in [2^-126, 2^128).  Seed: the exponent and top 20
+// mantissa bits of r2 are moved into an FP32 word with integer operations,
+// the SFU gives rsqrt.approx, and the result is moved back the same way
+// (relative seed error below 2^-19).  One third-order step
+//   y = y0 (1 + e/2 + 3 e^2/8),  e = 1 - r2 y0^2
+// (the binomial series of (1 - e)^{-1/2}) leaves a truncation error of about
+// (5/16) e^3 < 2^-55; y0 has 21 significant bits, so y0^2 is exact.  Five FP64
+// operations, none of them on the seed.
+__device__ __forceinline__ double rsqrt_f64(double r2) {
+    const int hi = __double2hiint(r2);
+    const float f = __int_as_float((hi - 0x38000000) << 3);
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(f));
+    const double y0 = __hiloint2double((__float_as_int(yf) >> 3) + 0x38000000, 0);
+    const double y2 = y0 * y0;
+    const double e = fma(-r2, y2, 1.0);
+    const double p = fma(e, 0.375, 0.5);
+    const double t = y0 * e;
+    return fma(t, p, y0);
+}
+
+// ------------------------------------------------------- float-float (EX)
+// A value is hi + lo with |lo| <= ulp(hi)/2 (Dekker 1971; Knuth TAOCP 2;
+// Hida, Li & Bailey 2001 for the double-double algorithms, here on floats).
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_make(float h, float l) { return ff{h, l}; }
+
+// exact: s + e = a + b (Knuth TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// exact when |a| >= |b| (Dekker FastTwoSum)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ ff ff_renorm(float s, float e) {
+    ff r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return ff_renorm(s, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+// product, error terms folded with FMA (Dekker TwoProduct via FMA)
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ff_renorm(p, e);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return ff_renorm(p, e);
+}
+__device__ __forceinline__ ff ff_sqr(ff a) {
+    const float p = __fmul_rn(a.hi, a.hi);
+    float e = __fmaf_rn(a.hi, a.hi, -p);
+    e = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, e);
+    return ff_renorm(p, e);
+}
+// acc += a * b, product and sum kept exact to float-float accuracy
+__device__ __forceinline__ void ff_fma_acc(ff &acc, ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);
+    pe = __fmaf_rn(a.hi, b.lo, pe);
+    pe = __fmaf_rn(a.lo, b.hi, pe);
+    float s, e;
+    two_sum(acc.hi, p, s, e);
+    e = __fadd_rn(e, __fadd_rn(acc.lo, pe));
+    acc = ff_renorm(s, e);
+}
+// dot products: high parts summed with exact TwoSum, all second-order terms
+// gathered in one float, one renormalisation at the end.
+__device__ __forceinline__ ff ff_dot3(const ff a[3], const ff b[3]) {
+    float p0 = __fmul_rn(a[0].hi, b[0].hi), p1 = __fmul_rn(a[1].hi, b[1].hi),
+          p2 = __fmul_rn(a[2].hi, b[2].hi);
+    float lo = __fmaf_rn(a[0].hi, b[0].hi, -p0);
+    lo = __fmaf_rn(a[1].hi, b[1].hi, -p1) + lo;
+    lo = __fmaf_rn(a[2].hi, b[2].hi, -p2) + lo;
+    lo = __fmaf_rn(a[0].hi, b[0].lo, lo);
+    lo = __fmaf_rn(a[0].lo, b[0].hi, lo);
+    lo = __fmaf_rn(a[1].hi, b[1].lo, lo);
+    lo = __fmaf_rn(a[1].lo, b[1].hi, lo);
+    lo = __fmaf_rn(a[2].hi, b[2].lo, lo);
+    lo = __fmaf_rn(a[2].lo, b[2].hi, lo);
+    float s, e;
+    two_sum(p0, p1, s, e);
+    lo = __fadd_rn(lo, e);
+    two_sum(s, p2, s, e);
+    lo = __fadd_rn(lo, e);
+    return ff_renorm(s, lo);
+}
+
+// ------------------------------------------------------------ TMA / mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared (TMA engine), completion counted in bytes on bar.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false after kWaitBudgetNs without completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitBudgetNs) return false;
+    }
+}
+
+// ------------------------------------------------------------ launchers
+// (implemented in the kernel translation units)
+cudaError_t launch_select_min(const Dev &d, cudaStream_t st);
+cudaError_t launch_select_compact(const Dev &d, double unused, cudaStream_t st);
+cudaError_t launch_predict(const Dev &d, int also64, int use_fixed_t, double t_fixed,
+                           cudaStream_t st);
+cudaError_t launch_pad(const Dev &d, cudaStream_t st);
+cudaError_t launch_eval(const Dev &d, int mode, const EvalLaunch &L, int grid, cudaStream_t st);
+cudaError_t launch_correct(const Dev &d, int64_t lo, int64_t hi, const int32_t *active,
+                           int32_t n_active, double t_next, const double *ajs, cudaStream_t st);
+cudaError_t launch_init_clear(const Dev &d, cudaStream_t st);
+cudaError_t launch_energy(const Dev &d, int64_t begin, int64_t end, int blocks, cudaStream_t st);
+cudaError_t launch_fill_identity(const Dev &d, cudaStream_t st);
+int eval_occupancy(int precision, int mode);  // CTAs per SM
+
+}  // namespace nb
