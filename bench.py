@@ -230,11 +230,18 @@ def gpu_arm(args, ws, rank, local):
         inter_all = float(ii.item())
     value = inter_all / (ms_max * 1e-3)
 
-    # ---- EX and FP32 on the same slices (shorter), and the e2e number
+    # ---- EX on the same slices (shorter); per-precision evaluation kernel rates
+    # on the same system (FP32 block-step runs are not used: its force noise
+    # makes the interpolated 6th-order derivatives collapse the time steps);
+    # and the end-to-end number through the C ABI with host buffers.
     k2 = max(1, min(args.steps, args.other_steps))
-    rex = run_precision("ex", k2, args.warmup, False)
-    r32 = run_precision("fp32", k2, args.warmup, False)
-    e2e_val, state_bytes = e2e_run(max(1, min(args.steps, args.other_steps)), args.warmup)
+    rex = run_precision("ex", k2, args.warmup, False) if not args.only_fp64 else None
+    kern = {}
+    if not args.only_fp64:
+        for prec in ("fp64", "ex", "fp32"):
+            kern[prec] = {f"A={a}": eval_rate(nb, torch, dev, m, x, v, prec, a, 2 if a == N else 10)
+                          for a in (1024, N)}
+    e2e_val, state_bytes = (e2e_run(k2, args.warmup) if not args.only_fp64 else (None, 0))
 
     eval_avg_ms = r64["eval_ms"] / max(r64["eval_launches"], 1)
     # algorithmic flops of the evaluation launches in the timed region
@@ -267,14 +274,15 @@ def gpu_arm(args, ws, rank, local):
                      "share_of_step_time": r64["eval_ms"] / r64["ms"] if r64["ms"] else None,
                      "flops_per_interaction": FLOPS_PER_INTERACTION},
         "precisions": {
-            "f64": {"value": value, "steps": args.steps},
-            "ex": {"value": rate(rex), "steps": k2, "speedup_vs_f64": rate(rex) / rate(r64),
-                   "pct_fp32_peak_79": 100 * rate(rex) * FLOPS_PER_INTERACTION / peak32},
-            "f32": {"value": rate(r32), "steps": k2, "speedup_vs_f64": rate(r32) / rate(r64),
-                    "pct_fp32_peak_79": 100 * rate(r32) * FLOPS_PER_INTERACTION / peak32},
+            "block_steps": {"f64": value,
+                            "ex": None if rex is None else rate(rex),
+                            "ex_speedup_vs_f64": None if rex is None else rate(rex) / rate(r64),
+                            "f32": "not run: FP32 force noise collapses the 6th-order time steps",
+                            "slices_ex": k2},
+            "eval_kernel": kern,
         },
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes, "steps": max(1, min(args.steps, args.other_steps)),
+                "d2h_bytes_per_step": state_bytes, "steps": k2,
                 "api": "nb_set_state(host) + nb_run + nb_get_state(host)"},
         "gpu_launches": r64["kernel_launches"],
         "clocks": clk,
@@ -287,6 +295,46 @@ def gpu_arm(args, ws, rank, local):
         import torch.distributed as dist
         dist.destroy_process_group()
     return out
+
+
+def eval_rate(nb, torch, dev, m, x, v, precision, A, reps):
+    """Evaluation-kernel throughput: A active particles against all N of the
+    start-up state (nb_predict then nb_evaluate), CUDA events on the stream."""
+    n = len(m)
+    sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX,
+                        precision=precision)
+    sim.predict(0.0, out=False)
+    act = torch.arange(A, dtype=torch.int32, device=dev)
+    out = torch.empty((10, A), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    nb.nb_evaluate(sim.ctx, 0, act, A, out)          # warm-up launch
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        nb.nb_evaluate(sim.ctx, 0, act, A, out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sim.sync()
+    sim.close()
+    ms = e0.elapsed_time(e1) / reps
+    return {"interactions_per_s": A * (n - 1) / (ms * 1e-3), "ms_per_launch": ms}
+
+
+def eval_case(args):
+    """--case eval: one evaluation launch size, for kernel profiling."""
+    import torch
+    from paper_1812_00367_gb300 import build as nbbuild
+    from paper_1812_00367_gb300 import ic, nb
+    nbbuild.build()
+    nb.load()
+    dev = torch.device("cuda", 0)
+    m, x, v = ic.plummer(args.n, seed=SEED)
+    r = eval_rate(nb, torch, dev, m, x, v, args.precision, args.active, args.reps)
+    print(json.dumps({"case": "eval", "precision": args.precision, "n": args.n,
+                      "active": args.active, **r,
+                      "gflops_79": r["interactions_per_s"] * FLOPS_PER_INTERACTION / 1e9}))
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -364,7 +412,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-interactions", type=float, default=5e8)
+    ap.add_argument("--only-fp64", action="store_true", help="headline run only (profiling)")
+    ap.add_argument("--case", choices=["run", "eval"], default="run")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "ex", "fp32"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--active", type=int, default=N)
+    ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args()
+    if args.case == "eval":
+        eval_case(args)
+        return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
     if args.impl == "reference":

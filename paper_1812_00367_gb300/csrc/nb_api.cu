@@ -212,8 +212,7 @@ void plan_direct(const nb_ctx *ctx, int cluster, int32_t n_active, int &gl, int 
     tiles = (int)cdiv(n_active, kTPB / gl);
     const int64_t ncl = ctx->h_offsets[cluster + 1] - ctx->h_offsets[cluster];
     const int64_t ntj = cdiv(ncl, kTJ);
-    int64_t S = cdiv(e.target_items, std::max(tiles, 1));
-    S = std::max<int64_t>(1, std::min<int64_t>(S, ntj));
+    int64_t S = choose_split(tiles, ntj, e.target_items, ctx->grid_eval);
     if (S > 1 && (int64_t)tiles * S > ctx->cap_items) S = std::max<int64_t>(1, ctx->cap_items / tiles);
     split = (int)S;
 }
@@ -401,6 +400,7 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     ALLOC(d.active, n);
     ALLOC(d.plan, n_clusters);
     ALLOC(d.n_items, 1);
+    ALLOC(d.item_ctr, 1);
     ALLOC(ctx->d_table, kBuckets);
     ALLOC(d.partial, ctx->cap_items * 10 * kTPB);
     const int64_t max_tiles = n + n_clusters + 1;
@@ -689,7 +689,7 @@ nb_status nb_autotune(nb_ctx *ctx, const char *cache_path) {
             for (int b = 0; okc && b < kBuckets; ++b)
                 if (std::fscanf(f, "%d %d", &t[b].gl, &t[b].target_items) != 2) okc = 0;
             std::fclose(f);
-            if (okc && prec == ctx->p.precision && grid == ctx->grid_eval) {
+            if (okc && prec == ctx->p.precision) {
                 ctx->table = t;
                 return upload_table(ctx);
             }

@@ -3,16 +3,16 @@
 // of Nitadori & Makino 2008) in three arithmetics, plus its j-split reduction.
 //
 // Per pair, with r = x_j - x_i, v = v_j - v_i, a = a_j - a_i (predicted),
-// y = (r.r + eps^2)^{-1/2}, q = m_j y^3, alpha = (r.v) y^2, zeta = (v.v + r.a) y^2:
-//   A0 = q r
-//   A1 = q v - 3 alpha A0                = q v - 3 (q alpha) r
-//   A2 = q a - 6 alpha A1 - 3 beta A0    = q a - 6 (q alpha) v + 3 q (5 alpha^2 - zeta) r
-// (beta = zeta + alpha^2).  The six sums
-//   sum q r, sum q v, sum q alpha r, sum q a, sum q alpha v, sum q (5 alpha^2 - zeta) r
-// are accumulated separately and combined once per (i, j-range):
-//   acc = S_qr, jerk = S_qv - 3 S_qar, snap = S_qa - 6 S_qav + 3 S_qcr, pot = -sum m_j y.
-// That keeps every per-pair operation a multiply or a fused multiply-add
-// (54 FP64 instructions per pair on the FP64 path).
+// y = (r.r + eps^2)^{-1/2}, q = m_j y^3, alpha = (r.v) y^2, zeta = (v.v + r.a) y^2,
+// beta = zeta + alpha^2:
+//   w1 = v - 3 alpha r,            A1 = q w1         (jerk term)
+//   w2 = a - 6 alpha w1 - 3 beta r, A2 = q w2         (snap term)
+//   A0 = q r,  pot -= m_j y
+// i.e. NM08's A1 = m v/s^3 - 3 alpha A0 and A2 = m a/s^3 - 6 alpha A1 - 3 beta A0
+// with the large alpha terms cancelling inside each pair before it is summed
+// (that keeps the FP32 path within its bound on strongly cancelling sums).
+// Every per-pair operation is a multiply, an add or a fused multiply-add:
+// 54 FP64 instructions per pair on the FP64 path.
 //
 // Work decomposition: a work item is (cluster, i-tile, j-range).  An i-tile
 // holds kTPB / gl active particles; gl lanes of a warp share one i and take
@@ -41,7 +41,7 @@ struct Prec<NB_FP64> {
         double x[3], v[3], a[3];
     };
     struct Acc {
-        double qr[3], qv[3], qar[3], qa[3], qav[3], qcr[3], p;
+        double a[3], j[3], s[3], p;
     };
     static __device__ __forceinline__ I load_i(const J *jarr, int64_t k) {
         const J e = jarr[k];
@@ -53,7 +53,7 @@ struct Prec<NB_FP64> {
     }
     static __device__ __forceinline__ void zero(Acc &c) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) c.qr[k] = c.qv[k] = c.qar[k] = c.qa[k] = c.qav[k] = c.qcr[k] = 0.0;
+        for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = 0.0;
         c.p = 0.0;
     }
     static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self,
@@ -75,15 +75,16 @@ struct Prec<NB_FP64> {
         const double w = fma(vx, vx, fma(vy, vy, fma(vz, vz, fma(rx, ax, fma(ry, ay, rz * az)))));
         const double al = rv * y2;
         const double ze = w * y2;
-        const double qa = q * al;
-        const double cc = fma(al * 5.0, al, -ze);
-        const double qc = q * cc;
-        c.qr[0] = fma(q, rx, c.qr[0]); c.qr[1] = fma(q, ry, c.qr[1]); c.qr[2] = fma(q, rz, c.qr[2]);
-        c.qv[0] = fma(q, vx, c.qv[0]); c.qv[1] = fma(q, vy, c.qv[1]); c.qv[2] = fma(q, vz, c.qv[2]);
-        c.qar[0] = fma(qa, rx, c.qar[0]); c.qar[1] = fma(qa, ry, c.qar[1]); c.qar[2] = fma(qa, rz, c.qar[2]);
-        c.qa[0] = fma(q, ax, c.qa[0]); c.qa[1] = fma(q, ay, c.qa[1]); c.qa[2] = fma(q, az, c.qa[2]);
-        c.qav[0] = fma(qa, vx, c.qav[0]); c.qav[1] = fma(qa, vy, c.qav[1]); c.qav[2] = fma(qa, vz, c.qav[2]);
-        c.qcr[0] = fma(qc, rx, c.qcr[0]); c.qcr[1] = fma(qc, ry, c.qcr[1]); c.qcr[2] = fma(qc, rz, c.qcr[2]);
+        const double al3 = 3.0 * al;
+        const double be3 = 3.0 * fma(al, al, ze);  // 3 beta
+        const double al6 = al3 + al3;
+        const double w1x = fma(-al3, rx, vx), w1y = fma(-al3, ry, vy), w1z = fma(-al3, rz, vz);
+        const double w2x = fma(-be3, rx, fma(-al6, w1x, ax));
+        const double w2y = fma(-be3, ry, fma(-al6, w1y, ay));
+        const double w2z = fma(-be3, rz, fma(-al6, w1z, az));
+        c.a[0] = fma(q, rx, c.a[0]); c.a[1] = fma(q, ry, c.a[1]); c.a[2] = fma(q, rz, c.a[2]);
+        c.j[0] = fma(q, w1x, c.j[0]); c.j[1] = fma(q, w1y, c.j[1]); c.j[2] = fma(q, w1z, c.j[2]);
+        c.s[0] = fma(q, w2x, c.s[0]); c.s[1] = fma(q, w2y, c.s[1]); c.s[2] = fma(q, w2z, c.s[2]);
     }
     // pot-only pair term (energy diagnostics)
     static __device__ __forceinline__ void interact_pot(const I &i, const J &jj, bool self,
@@ -96,13 +97,12 @@ struct Prec<NB_FP64> {
         m = self ? 0.0 : m;
         c.p = fma(m, rsqrt_f64(r2), c.p);
     }
-    static __device__ __forceinline__ void tile_done(Acc &, double *, int) {}
     static __device__ __forceinline__ void finish(const Acc &c, const double *, double o[10]) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            o[k] = c.qr[k];
-            o[3 + k] = fma(-3.0, c.qar[k], c.qv[k]);
-            o[6 + k] = fma(3.0, c.qcr[k], fma(-6.0, c.qav[k], c.qa[k]));
+            o[k] = c.a[k];
+            o[3 + k] = c.j[k];
+            o[6 + k] = c.s[k];
         }
         o[9] = -c.p;
     }
@@ -116,7 +116,7 @@ struct Prec<NB_EX> {
         ff x[3], v[3], a[3];
     };
     struct Acc {
-        ff qr[3], qv[3], qar[3], qa[3], qav[3], qcr[3], p;
+        ff a[3], j[3], s[3], p;
     };
     static __device__ __forceinline__ I load_i(const J *jarr, int64_t k) {
         const J e = jarr[k];
@@ -128,8 +128,7 @@ struct Prec<NB_EX> {
     }
     static __device__ __forceinline__ void zero(Acc &c) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-            c.qr[k] = c.qv[k] = c.qar[k] = c.qa[k] = c.qav[k] = c.qcr[k] = ff{0.f, 0.f};
+        for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = ff{0.f, 0.f};
         c.p = ff{0.f, 0.f};
     }
     // 1/sqrt(r2) in float-float: SFU seed y0, residual e = 1 - r2 y0^2 from the
@@ -175,27 +174,25 @@ struct Prec<NB_EX> {
         const ff w = ff_add(ff_dot3(v, v), ff_dot3(r, a));
         const ff al = ff_mul(rv, y2);
         const ff ze = ff_mul(w, y2);
-        const ff qa = ff_mul(q, al);
-        const ff cc = ff_sub(ff_mul(ff_mul_f(al, 5.0f), al), ze);
-        const ff qc = ff_mul(q, cc);
+        const ff al3 = ff_mul_f(al, 3.0f);
+        const ff be3 = ff_mul_f(ff_add(ff_sqr(al), ze), 3.0f);
+        const ff al6 = ff{2.0f * al3.hi, 2.0f * al3.lo};  // exact
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            ff_fma_acc(c.qr[k], q, r[k]);
-            ff_fma_acc(c.qv[k], q, v[k]);
-            ff_fma_acc(c.qar[k], qa, r[k]);
-            ff_fma_acc(c.qa[k], q, a[k]);
-            ff_fma_acc(c.qav[k], qa, v[k]);
-            ff_fma_acc(c.qcr[k], qc, r[k]);
+            const ff w1 = ff_fnma(al3, r[k], v[k]);
+            const ff w2 = ff_fnma(be3, r[k], ff_fnma(al6, w1, a[k]));
+            ff_fma_acc(c.a[k], q, r[k]);
+            ff_fma_acc(c.j[k], q, w1);
+            ff_fma_acc(c.s[k], q, w2);
         }
     }
-    static __device__ __forceinline__ void tile_done(Acc &, double *, int) {}
     static __device__ __forceinline__ double to_d(ff a) { return (double)a.hi + (double)a.lo; }
     static __device__ __forceinline__ void finish(const Acc &c, const double *, double o[10]) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            o[k] = to_d(c.qr[k]);
-            o[3 + k] = fma(-3.0, to_d(c.qar[k]), to_d(c.qv[k]));
-            o[6 + k] = fma(3.0, to_d(c.qcr[k]), fma(-6.0, to_d(c.qav[k]), to_d(c.qa[k])));
+            o[k] = to_d(c.a[k]);
+            o[3 + k] = to_d(c.j[k]);
+            o[6 + k] = to_d(c.s[k]);
         }
         o[9] = -to_d(c.p);
     }
@@ -209,7 +206,7 @@ struct Prec<NB_FP32> {
         float xh[3], xl[3], vh[3], vl[3], a[3];
     };
     struct Acc {
-        float qr[3], qv[3], qar[3], qa[3], qav[3], qcr[3], p;
+        float a[3], j[3], s[3], p;
     };
     static __device__ __forceinline__ I load_i(const J *jarr, int64_t k) {
         const J e = jarr[k];
@@ -223,7 +220,7 @@ struct Prec<NB_FP32> {
     }
     static __device__ __forceinline__ void zero(Acc &c) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) c.qr[k] = c.qv[k] = c.qar[k] = c.qa[k] = c.qav[k] = c.qcr[k] = 0.f;
+        for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = 0.f;
         c.p = 0.f;
     }
     static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self, double,
@@ -251,24 +248,24 @@ struct Prec<NB_FP32> {
         const float w = fmaf(vx, vx, fmaf(vy, vy, fmaf(vz, vz, fmaf(rx, ax, fmaf(ry, ay, rz * az)))));
         const float al = rv * y2;
         const float ze = w * y2;
-        const float qa = q * al;
-        const float cc = fmaf(al * 5.f, al, -ze);
-        const float qc = q * cc;
-        c.qr[0] = fmaf(q, rx, c.qr[0]); c.qr[1] = fmaf(q, ry, c.qr[1]); c.qr[2] = fmaf(q, rz, c.qr[2]);
-        c.qv[0] = fmaf(q, vx, c.qv[0]); c.qv[1] = fmaf(q, vy, c.qv[1]); c.qv[2] = fmaf(q, vz, c.qv[2]);
-        c.qar[0] = fmaf(qa, rx, c.qar[0]); c.qar[1] = fmaf(qa, ry, c.qar[1]); c.qar[2] = fmaf(qa, rz, c.qar[2]);
-        c.qa[0] = fmaf(q, ax, c.qa[0]); c.qa[1] = fmaf(q, ay, c.qa[1]); c.qa[2] = fmaf(q, az, c.qa[2]);
-        c.qav[0] = fmaf(qa, vx, c.qav[0]); c.qav[1] = fmaf(qa, vy, c.qav[1]); c.qav[2] = fmaf(qa, vz, c.qav[2]);
-        c.qcr[0] = fmaf(qc, rx, c.qcr[0]); c.qcr[1] = fmaf(qc, ry, c.qcr[1]); c.qcr[2] = fmaf(qc, rz, c.qcr[2]);
+        const float al3 = 3.f * al;
+        const float be3 = 3.f * fmaf(al, al, ze);
+        const float al6 = al3 + al3;
+        const float w1x = fmaf(-al3, rx, vx), w1y = fmaf(-al3, ry, vy), w1z = fmaf(-al3, rz, vz);
+        const float w2x = fmaf(-be3, rx, fmaf(-al6, w1x, ax));
+        const float w2y = fmaf(-be3, ry, fmaf(-al6, w1y, ay));
+        const float w2z = fmaf(-be3, rz, fmaf(-al6, w1z, az));
+        c.a[0] = fmaf(q, rx, c.a[0]); c.a[1] = fmaf(q, ry, c.a[1]); c.a[2] = fmaf(q, rz, c.a[2]);
+        c.j[0] = fmaf(q, w1x, c.j[0]); c.j[1] = fmaf(q, w1y, c.j[1]); c.j[2] = fmaf(q, w1z, c.j[2]);
+        c.s[0] = fmaf(q, w2x, c.s[0]); c.s[1] = fmaf(q, w2y, c.s[1]); c.s[2] = fmaf(q, w2z, c.s[2]);
     }
-    // Promote the FP32 chunk sums (combined to acc/jerk/snap/pot) into the
-    // FP64 totals and restart the FP32 sums.
+    // Promote the FP32 chunk sums into the FP64 totals and restart them.
     static __device__ __forceinline__ void flush(Acc &c, double *t64) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            t64[k] += (double)c.qr[k];
-            t64[3 + k] += (double)fmaf(-3.f, c.qar[k], c.qv[k]);
-            t64[6 + k] += (double)fmaf(3.f, c.qcr[k], fmaf(-6.f, c.qav[k], c.qa[k]));
+            t64[k] += (double)c.a[k];
+            t64[3 + k] += (double)c.j[k];
+            t64[6 + k] += (double)c.s[k];
         }
         t64[9] += (double)c.p;
         zero(c);
@@ -285,8 +282,10 @@ struct Prec<NB_FP32> {
 template <int P>
 struct SmemLayout {
     typename Prec<P>::J tile[kStages][kTJ];
+    double red[10 * kTPB];  // cross-split reduction: group sums, then totals
     uint64_t bar[kStages];
     int flag;
+    long long next_item;
     int fail;
 };
 
@@ -321,8 +320,20 @@ __device__ __forceinline__ void finalize_one(const Dev &d, const EvalLaunch &L, 
     }
 }
 
+// Next work item of this CTA (see the item loop of k_eval).  Ends with a
+// barrier, so the shared slot can be reused.
+template <int P>
+__device__ __forceinline__ int64_t next_item_of(const EvalLaunch &L, const Dev &d, SmemLayout<P> &S,
+                                                int64_t item) {
+    if (L.direct) return item + gridDim.x;
+    __syncthreads();
+    if (threadIdx.x == 0) S.next_item = (long long)atomicAdd(d.item_ctr, 1ull);
+    __syncthreads();
+    return S.next_item;
+}
+
 template <int P, int MODE>
-__global__ void __launch_bounds__(kTPB) k_eval(const Dev d, const EvalLaunch L) {
+__global__ void __launch_bounds__(kTPB, 4) k_eval(const Dev d, const EvalLaunch L) {
     using T = Prec<P>;
     using J = typename T::J;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -346,7 +357,17 @@ __global__ void __launch_bounds__(kTPB) k_eval(const Dev d, const EvalLaunch L) 
     uint32_t phase = 0;   // bit s: parity of stage s
     uint32_t pending = 0; // bit s: a copy into stage s is in flight
 
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    // Items: direct launches (equal-cost items of one cluster) take a static
+    // round robin; planned launches fetch items dynamically, since clusters of
+    // a batch give items of unequal cost.  Either way an item's arithmetic and
+    // the split-order reduction do not depend on the CTA that runs it.
+    int64_t item = blockIdx.x;
+    if (!L.direct) {
+        if (tid == 0) S.next_item = (long long)atomicAdd(d.item_ctr, 1ull);
+        __syncthreads();
+        item = S.next_item;
+    }
+    for (; item < n_items;) {
         int c, gl, split, A;
         int64_t item0, tile0, pslot0;
         if (L.direct) {
@@ -459,6 +480,7 @@ __global__ void __launch_bounds__(kTPB) k_eval(const Dev d, const EvalLaunch L) 
 
         if (split == 1) {
             if (valid && jsub == 0 && !bad_index) finalize_one<P, MODE>(d, L, c, gi, iloc, o);
+            item = next_item_of<P>(L, d, S, item);
             continue;
         }
         double *part = d.partial + (pslot0 + local) * (int64_t)(10 * kTPB);
@@ -474,29 +496,45 @@ __global__ void __launch_bounds__(kTPB) k_eval(const Dev d, const EvalLaunch L) 
         }
         __syncthreads();
         if (S.flag) {
+            // Last CTA of this i-tile: add the split partials of every (i, q)
+            // pair in two fixed-order levels.  Level 1: thread (p, r) sums the
+            // r-th contiguous group of splits of pair p in split order; level 2
+            // adds the R group sums in group order.  The order depends only on
+            // (split, valid i count), so results are reproducible.
             __threadfence();
-            if (tid < Ti) {
-                const int il = tile * Ti + tid;
-                if (il < A) {
-                    double sum[10];
+            const int nv = min(Ti, A - tile * Ti);     // valid i in this tile
+            const int npair = nv * 10;
+            const int R = max(1, kTPB / npair);
+            const double *base = d.partial + (pslot0 + (int64_t)tile * split) * (10 * kTPB);
+            for (int w = tid; w < npair * R; w += kTPB) {
+                const int p = w % npair, r = w / npair;
+                const int q = p / nv, il = p % nv;
+                const int s0 = (int)((int64_t)split * r / R), s1 = (int)((int64_t)split * (r + 1) / R);
+                double acc = 0.0;
+#pragma unroll 4
+                for (int sp = s0; sp < s1; ++sp) acc += __ldcg(base + (int64_t)sp * (10 * kTPB) + q * kTPB + il);
+                S.red[r * npair + p] = acc;
+            }
+            __syncthreads();
+            if (tid < nv) {
+                double sum[10];
 #pragma unroll
-                    for (int q = 0; q < 10; ++q) sum[q] = 0.0;
-                    const double *base = d.partial + (pslot0 + (int64_t)tile * split) * (10 * kTPB);
-                    for (int sp = 0; sp < split; ++sp) {
-                        const double *pp = base + (int64_t)sp * (10 * kTPB);
-#pragma unroll
-                        for (int q = 0; q < 10; ++q) sum[q] += __ldcg(pp + q * kTPB + tid);
-                    }
-                    int64_t g2;
-                    if (L.identity) g2 = off + il;
-                    else if (L.direct) g2 = L.active[il];
-                    else g2 = d.active[off + il];
-                    if (g2 >= off && g2 < off + nc) finalize_one<P, MODE>(d, L, c, g2, il, sum);
+                for (int q = 0; q < 10; ++q) {
+                    double acc = 0.0;
+                    for (int r = 0; r < R; ++r) acc += S.red[r * npair + q * nv + tid];
+                    sum[q] = acc;
                 }
+                const int il = tile * Ti + tid;
+                int64_t g2;
+                if (L.identity) g2 = off + il;
+                else if (L.direct) g2 = L.active[il];
+                else g2 = d.active[off + il];
+                if (g2 >= off && g2 < off + nc) finalize_one<P, MODE>(d, L, c, g2, il, sum);
             }
             if (tid == 0) d.tile_cnt[tile0 + tile] = 0;
         }
         __syncthreads();
+        item = next_item_of<P>(L, d, S, item);
     }
 }
 

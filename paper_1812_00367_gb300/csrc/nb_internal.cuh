@@ -88,6 +88,7 @@ struct Dev {
     // plan
     ClusterPlan *plan; // [nc]
     int64_t *n_items;  // [1]
+    unsigned long long *item_ctr;  // [1]: next work item (dynamic fetch), reset by k_plan
     const PlanEntry *table;  // [kBuckets]
     // reduction scratch
     double *partial;   // [max_items][10][kTPB]
@@ -124,6 +125,39 @@ enum EvalMode { kModeOut = 0, kModeStep = 1, kModeInit1 = 2, kModeInit2 = 3, kMo
 
 // ---------------------------------------------------------- small helpers
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+constexpr int kMinTilesPerItem = 4;  // a j-range holds at least 4 x 64 j
+
+// Number of j-ranges (split S) for `tiles` i-tiles over a cluster of `ntj`
+// j-tiles.  Start from the bucket's target item count; keep at least
+// kMinTilesPerItem j-tiles per item; for `grid` resident CTAs, take the
+// smallest S in [S0/2, 2 S0] whose items fill the largest fraction of whole
+// waves (equal-cost items: a last, partly filled wave leaves SMs idle).  The
+// result depends on this cluster alone, so a cluster's plan (and therefore
+// its rounding) is the same in a batch as on its own.
+__host__ __device__ inline int64_t choose_split(int64_t tiles, int64_t ntj, int64_t target,
+                                                int64_t grid) {
+    const int64_t smax = ntj / kMinTilesPerItem > 1 ? ntj / kMinTilesPerItem : 1;
+    int64_t s0 = cdiv(target, tiles > 0 ? tiles : 1);
+    s0 = s0 < 1 ? 1 : (s0 > smax ? smax : s0);
+    if (grid <= 0) return s0;
+    // efficiency items / (waves * grid), compared by cross-multiplication in
+    // integers (FP64 divisions are slow on this part, and this runs in one
+    // thread of the planner)
+    int64_t best = s0, best_items = 0, best_slots = 1;
+    const int64_t lo = s0 / 2 > 1 ? s0 / 2 : 1;
+    const int64_t hi = 2 * s0 < smax ? 2 * s0 : smax;
+    for (int64_t s = lo; s <= hi; ++s) {
+        const int64_t items = tiles * s;
+        const int64_t slots = cdiv(items, grid) * grid;
+        if (items * best_slots > best_items * slots) {
+            best_items = items;
+            best_slots = slots;
+            best = s;
+        }
+    }
+    return best;
+}
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -216,6 +250,17 @@ __device__ __forceinline__ void ff_fma_acc(ff &acc, ff a, ff b) {
     two_sum(acc.hi, p, s, e);
     e = __fadd_rn(e, __fadd_rn(acc.lo, pe));
     acc = ff_renorm(s, e);
+}
+// a - b*c: the product's error terms folded by FMA, one renormalisation
+__device__ __forceinline__ ff ff_fnma(ff b, ff c, ff a) {
+    const float p = __fmul_rn(b.hi, c.hi);
+    float pe = __fmaf_rn(b.hi, c.hi, -p);
+    pe = __fmaf_rn(b.hi, c.lo, pe);
+    pe = __fmaf_rn(b.lo, c.hi, pe);
+    float s, e;
+    two_sum(a.hi, -p, s, e);
+    e = __fadd_rn(e, __fsub_rn(a.lo, pe));
+    return ff_renorm(s, e);
 }
 // dot products: high parts summed with exact TwoSum, all second-order terms
 // gathered in one float, one renormalisation at the end.

@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan(const Dev d, int mode_init, i
                     const PlanEntry e = d.table[31 - __clz(A)];
                     tiles = cdiv(A, kTPB / e.gl);
                     const long long ntj = cdiv(ncl, kTJ);
-                    long long S = fallback ? 1 : cdiv(e.target_items, tiles);
-                    S = S < 1 ? 1 : (S > ntj ? ntj : S);
+                    const long long S =
+                        fallback ? 1 : choose_split(tiles, ntj, e.target_items, d.grid_eval);
                     items = tiles * S;
                     pl = ClusterPlan{e.gl, (int)S, (int)tiles, A, 0, 0, 0};
                     my_inter = (double)A * (double)(ncl - 1);
@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan(const Dev d, int mode_init, i
         if (!fallback && carry_slots > d.partial_items) continue;
         if (tid == 0) {
             *d.n_items = carry_items;
+            *d.item_ctr = 0ull;
             *d.busy = (int)busy;
             if (count && !mode_init) {
                 *d.ctr_steps += (unsigned long long)busy;
@@ -205,14 +206,16 @@ __device__ __forceinline__ void split_ff(double x, float &hi, float &lo) {
 
 __global__ void __launch_bounds__(kSelTPB) k_predict(const Dev d, int also64, int use_fixed,
                                                      double t_fixed) {
-    const int k = blockIdx.x;
+    // kChunk / kSelTPB CTAs per chunk: one particle per thread, all SMs busy
+    constexpr int kSub = kChunk / kSelTPB;
+    const int k = blockIdx.x / kSub;
     const int c = d.chunk_cluster[k];
     if (!use_fixed && d.nact[c] == 0) return;  // idle cluster this step
     const double tn = use_fixed ? t_fixed : d.tnext[c];
     const int64_t off = d.offsets[c];
     const int64_t jo = d.jofs[c];
-    const int64_t b = d.chunk_begin[k], e = d.chunk_end[k];
-    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+    const int64_t b = d.chunk_begin[k] + (int64_t)(blockIdx.x % kSub) * kSelTPB, e = d.chunk_end[k];
+    for (int64_t i = b + threadIdx.x; i < e && i < b + kSelTPB; i += blockDim.x) {
         double xp[3], vp[3], ap[3];
         predict_particle(d, i, tn, xp, vp, ap);
         const double m = d.m[i];
@@ -381,7 +384,7 @@ cudaError_t launch_unpack64(const Dev &d, double *out, cudaStream_t st) {
 }
 cudaError_t launch_predict(const Dev &d, int also64, int use_fixed, double t_fixed,
                            cudaStream_t st) {
-    k_predict<<<d.n_chunks, kSelTPB, 0, st>>>(d, also64, use_fixed, t_fixed);
+    k_predict<<<d.n_chunks * (kChunk / kSelTPB), kSelTPB, 0, st>>>(d, also64, use_fixed, t_fixed);
     return cudaGetLastError();
 }
 cudaError_t launch_pad(const Dev &d, cudaStream_t st) {
