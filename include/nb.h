@@ -222,6 +222,38 @@ nb_status nb_get_counters(nb_ctx *ctx, nb_counters *out);
  */
 nb_status nb_autotune(nb_ctx *ctx, const char *cache_path);
 
+/*
+ * nb_evaluate_noalloc -- the FP64 evaluation of nb_evaluate for callers that
+ * cannot allocate device memory.  The paper has no counterpart.  Some callers
+ * cannot call cudaMalloc: code embedded in a framework whose memory pool
+ * already holds the device memory (a native allocation fails, or escapes the
+ * framework's accounting), and latency-critical loops that must not allocate
+ * (cudaMalloc can synchronise the whole device).  nb_init allocates scratch,
+ * so those callers cannot use nb_evaluate.
+ * This entry needs no context and allocates nothing: its working space (packed j
+ * tiles, split partial sums, tile counters; about 5.3 MB) is a fixed array
+ * compiled into the library, which every GPU that loads libnb keeps until the
+ * process exits.
+ *   jpred    : DEVICE double [10][n]: x[3], v[3], a[3], m of every particle
+ *              (the layout nb_predict writes to its `out`)
+ *   n        : 1 <= n <= 32768 (larger: NB_EINVAL)
+ *   eps      : softening length (>= 0)
+ *   active   : DEVICE int32 [n_active], indices in [0, n); 0 <= n_active <=
+ *              32768; duplicates allowed
+ *   out      : DEVICE double [10][n_active]: acc[3], jerk[3], snap[3], pot
+ *   stream   : cudaStream_t (NULL = legacy default); the call synchronises it
+ *              to read its error word
+ * The first call on a device looks up the array's device address with that
+ * device current (make that first call before any stream capture).  All
+ * calls share the array: calls that overlap on the GPU (other streams,
+ * threads or processes sharing the library) race and must be serialised by
+ * the caller.  Errors: NB_EINVAL (sizes, NULL pointers, an index outside
+ * [0, n): that entry is skipped and reported), NB_ECUDA, NB_ETIMEOUT;
+ * messages through nb_last_error(NULL).
+ */
+nb_status nb_evaluate_noalloc(const double *jpred, int64_t n, double eps, const int32_t *active,
+                              int32_t n_active, double *out, void *stream);
+
 /* nb_sync -- wait for the context's stream and check the device error word. */
 nb_status nb_sync(nb_ctx *ctx);
 

@@ -249,6 +249,11 @@ nb_status startup(nb_ctx *ctx) {
 }
 }  // namespace
 
+namespace nb {
+// Message for nb_last_error(NULL) from calls that have no context.
+void set_global_error(const char *msg) { g_init_err = msg; }
+}  // namespace nb
+
 // =================================================================== ABI
 extern "C" {
 
