@@ -134,9 +134,19 @@ def gpu_arm(args, ws, rank, local):
     peak32, _ = nb.nb_probe_fma_peak(nb.NB_FP32, 65536)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    import tempfile
+    tune_dir = tempfile.mkdtemp(prefix="nbtune_")
+
+    def tune(sim, precision):
+        """The autotuner picks lanes-per-i and splits per active-set size
+        before anything is timed (one table per arithmetic for this run)."""
+        if not args.no_autotune:
+            sim.autotune(os.path.join(tune_dir, f"{precision}.txt"))
+
     def run_precision(precision, steps, warmup, timed_eval):
         sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX,
                             precision=precision, time_eval=timed_eval)
+        tune(sim, precision)
         snap = {k: t.clone() for k, t in sim.buf.items()}
         stream = torch.cuda.current_stream(dev)
 
@@ -156,10 +166,10 @@ def gpu_arm(args, ws, rank, local):
             e0.record(stream)
             if slice_idx == 0 and k > 0:
                 restore()
-            _, inter = sim.run((slice_idx + 1) * SLICE)
+            _, inter = sim.run((slice_idx + 1) * args.slice)
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            slice_idx = (slice_idx + 1) % SLICES
+            slice_idx = (slice_idx + 1) % int(round(T_END / args.slice))
             if timed:
                 c1 = sim.counters()
                 ms_tot += e0.elapsed_time(e1)
@@ -177,6 +187,7 @@ def gpu_arm(args, ws, rank, local):
         the state in from pinned host memory, runs the slice, copies it back."""
         sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX,
                             precision="fp64")
+        tune(sim, "fp64")
         host0 = {}
         for f, t in sim.buf.items():
             host0[f] = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
@@ -198,10 +209,10 @@ def gpu_arm(args, ws, rank, local):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             nb.nb_set_state(sim.ctx, hst)
-            _, inter = sim.run((slice_idx + 1) * SLICE)
+            _, inter = sim.run((slice_idx + 1) * args.slice)
             nb.nb_get_state(sim.ctx, hst)
             t1 = time.perf_counter()
-            slice_idx = (slice_idx + 1) % SLICES
+            slice_idx = (slice_idx + 1) % int(round(T_END / args.slice))
             if timed:
                 inter_tot += inter
                 sec_tot += t1 - t0
@@ -218,16 +229,8 @@ def gpu_arm(args, ws, rank, local):
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
 
-    ms_max = r64["ms"]
-    inter_all = r64["interactions"]
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_max], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_max = float(tt.item())
-        ii = torch.tensor([inter_all], dtype=torch.float64, device=dev)
-        dist.all_reduce(ii, op=dist.ReduceOp.SUM)
-        inter_all = float(ii.item())
+    from paper_1812_00367_gb300.replicas import combine_timing
+    ms_max, inter_all = combine_timing(r64["ms"], r64["interactions"], dev)
     value = inter_all / (ms_max * 1e-3)
 
     # ---- EX on the same slices (shorter); per-precision evaluation kernel rates
@@ -256,9 +259,10 @@ def gpu_arm(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "eps": EPS, "eta": ETA, "dt_min": DT_MIN,
-                   "dt_max": DT_MAX, "t_end": T_END, "step": "1/64 N-body time slice",
+                   "dt_max": DT_MAX, "t_end": T_END, "step": f"{args.slice:g} N-body time slice",
                    "l2": "flushed (256 MB write) before each timed step",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "plan_table": "default" if args.no_autotune else "nb_autotune before timing",
                    "seed": SEED},
         "gflops_79": value * FLOPS_PER_INTERACTION / 1e9,
         "fp64_fma_peak_tflops_measured": peak64 / 1e12,
@@ -286,6 +290,10 @@ def gpu_arm(args, ws, rank, local):
                 "api": "nb_set_state(host) + nb_run + nb_get_state(host)"},
         "gpu_launches": r64["kernel_launches"],
         "clocks": clk,
+        # board power (nvidia-smi, median over the timed region) x time / work
+        "energy_nj_per_interaction": (None if not clk.get("power_w_median") else
+                                      clk["power_w_median"] * r64["ms"] * 1e-3
+                                      / r64["interactions"] * 1e9),
         "wall_s_timed_region": t_wall,
         "dt_underflows": r64["underflows"],
     }
@@ -301,8 +309,9 @@ def eval_rate(nb, torch, dev, m, x, v, precision, A, reps):
     """Evaluation-kernel throughput: A active particles against all N of the
     start-up state (nb_predict then nb_evaluate), CUDA events on the stream."""
     n = len(m)
+    # no start-up evaluations: the launches of this case are the timed ones
     sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX,
-                        precision=precision)
+                        precision=precision, keep_state=True)
     sim.predict(0.0, out=False)
     act = torch.arange(A, dtype=torch.int32, device=dev)
     out = torch.empty((10, A), dtype=torch.float64, device=dev)
@@ -335,6 +344,154 @@ def eval_case(args):
     print(json.dumps({"case": "eval", "precision": args.precision, "n": args.n,
                       "active": args.active, **r,
                       "gflops_79": r["interactions_per_s"] * FLOPS_PER_INTERACTION / 1e9}))
+
+
+def _timed_run(sim, torch, dev, t_end):
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    steps, inter = sim.run(t_end)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return steps, inter, e0.elapsed_time(e1) * 1e-3
+
+
+def batched_case(args):
+    """512 independent Plummer clusters, N log-uniform in [256, 16384], eps 1e-4,
+    each on its own block steps, all advanced together (one persistent
+    evaluation launch per block step, graph-replayed): FP64 and EX."""
+    import torch
+    from paper_1812_00367_gb300 import build as nbbuild
+    from paper_1812_00367_gb300 import ic, nb
+    nbbuild.build()
+    nb.load()
+    dev = torch.device("cuda", 0)
+    batch = ic.plummer_batch(args.clusters, seed=SEED)
+    out = {"case": "batched", "clusters": args.clusters, "n_total": int(batch.offsets[-1]),
+           "n_min": int(batch.sizes.min()), "n_max": int(batch.sizes.max()), "eps": EPS,
+           "t_warm": args.t_warm, "t_end": args.t_warm + args.t_run}
+    for prec in ("fp64", "ex"):
+        sim = nb.Simulation(batch.m, batch.x, batch.v, eps=EPS, eta=ETA, dt_min=DT_MIN,
+                            dt_max=DT_MAX, precision=prec, offsets=batch.offsets)
+        e0 = [sum(sim.energy(0.0, c)[:2]) for c in range(args.clusters)]
+        sim.run(args.t_warm)
+        steps, inter, sec = _timed_run(sim, torch, dev, args.t_warm + args.t_run)
+        t1 = args.t_warm + args.t_run
+        e1 = [sum(sim.energy(t1, c)[:2]) for c in range(args.clusters)]
+        drift = [abs(b - a) / abs(a) / t1 for a, b in zip(e0, e1)]
+        out[prec] = {"interactions_per_s": inter / sec, "seconds": sec, "cluster_block_steps": steps,
+                     "interactions": inter, "energy_drift_per_time_max": max(drift),
+                     "energy_drift_per_time_median": statistics.median(drift)}
+        sim.close()
+    out["ex_speedup_vs_f64"] = out["ex"]["interactions_per_s"] / out["fp64"]["interactions_per_s"]
+    print(json.dumps(out))
+
+
+def config3_case(args):
+    """Plummer N = 2^20 with Kroupa-like masses, eps = 1e-5: evaluation
+    throughput per arithmetic, a/j/s/pot errors on a 4096-particle subsample
+    against the FP64 oracle, and energy drift over a short block-step run."""
+    import torch
+    from oracle import nb_oracle
+    from paper_1812_00367_gb300 import build as nbbuild
+    from paper_1812_00367_gb300 import ic, nb
+    nbbuild.build()
+    nb.load()
+    nb_oracle.build()
+    dev = torch.device("cuda", 0)
+    n, eps = 1 << 20, 1e-5
+    masses = ic.kroupa_masses(n, seed=3)
+    m, x, v = ic.plummer(n, seed=3, masses=masses)
+    rng = np.random.default_rng(3)
+    sub = np.sort(rng.choice(n, 4096, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    ref = nb_oracle.force(m, x, v, np.zeros_like(x), eps, active=sub)
+    t_oracle = time.perf_counter() - t0
+    out = {"case": "config3", "n": n, "eps": eps, "subsample": len(sub),
+           "oracle_seconds_subsample": t_oracle, "oracle_threads": nb_oracle.num_threads()}
+    for prec in ("fp64", "ex", "fp32"):
+        sim = nb.Simulation(m, x, v, eps=eps, precision=prec, keep_state=True)
+        st = {"m": m, "x": x, "v": v, "a": np.zeros((n, 3)), "j": np.zeros((n, 3)),
+              "s": np.zeros((n, 3)), "c": np.zeros((n, 3)), "t": np.zeros(n),
+              "dt": np.full(n, 2.0 ** -6), "pot": np.zeros(n)}
+        sim.set_state_numpy(st)
+        sim.predict(0.0, out=False)
+        got = sim.evaluate(torch.as_tensor(sub, device=dev)).cpu().numpy()
+        errs = {}
+        for name, lo, r in (("a", 0, ref[0]), ("j", 3, ref[1]), ("s", 6, ref[2])):
+            e = np.linalg.norm(got[lo:lo + 3].T - r, axis=1) / np.linalg.norm(r, axis=1)
+            errs[name] = {"max": float(e.max()), "p99.9": float(np.quantile(e, 0.999))}
+        e = np.abs(got[9] - ref[3]) / np.abs(ref[3])
+        errs["pot"] = {"max": float(e.max()), "p99.9": float(np.quantile(e, 0.999))}
+        A = n if (prec != "fp64" or args.c3_full_fp64) else args.c3_active
+        act = torch.arange(A, dtype=torch.int32, device=dev)
+        o = torch.empty((10, A), dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        nb.nb_evaluate(sim.ctx, 0, act, A, o)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        sec = ev0.elapsed_time(ev1) * 1e-3
+        sim.close()
+        out[prec] = {"errors": errs, "eval_active": A, "eval_seconds": sec,
+                     "interactions_per_s": A * (n - 1) / sec,
+                     "gflops_79": A * (n - 1) / sec * FLOPS_PER_INTERACTION / 1e9}
+    if args.c3_run_t > 0:
+        for prec in args.c3_run_precisions.split(","):
+            sim = nb.Simulation(m, x, v, eps=eps, precision=prec)
+            E0 = sum(sim.energy(0.0)[:2])
+            steps, inter, sec = _timed_run(sim, torch, dev, args.c3_run_t)
+            E1 = sum(sim.energy(args.c3_run_t)[:2])
+            c = sim.counters()
+            out[prec]["block_run"] = {"t_end": args.c3_run_t, "block_steps": steps,
+                                      "interactions_per_s": inter / sec, "seconds": sec,
+                                      "energy_drift_per_time": abs(E1 - E0) / abs(E0) / args.c3_run_t,
+                                      "dt_underflows": c["dt_underflows"]}
+            sim.close()
+    print(json.dumps(out))
+
+
+def merger_case(args):
+    """Two Hernquist spheres of 2^21 particles each on a parabolic orbit,
+    eps = 1e-3: evaluation throughput of an active subset against all
+    4,194,304 particles in FP64 and EX."""
+    import torch
+    from paper_1812_00367_gb300 import build as nbbuild
+    from paper_1812_00367_gb300 import ic, nb
+    nbbuild.build()
+    nb.load()
+    dev = torch.device("cuda", 0)
+    m, x, v = ic.hernquist_merger(1 << 21, seed=5)
+    n = len(m)
+    out = {"case": "merger", "n": n, "eps": 1e-3, "active": args.merger_active}
+    for prec in ("fp64", "ex", "fp32"):
+        sim = nb.Simulation(m, x, v, eps=1e-3, precision=prec, keep_state=True)
+        st = {"m": m, "x": x, "v": v, "a": np.zeros((n, 3)), "j": np.zeros((n, 3)),
+              "s": np.zeros((n, 3)), "c": np.zeros((n, 3)), "t": np.zeros(n),
+              "dt": np.full(n, 2.0 ** -6), "pot": np.zeros(n)}
+        sim.set_state_numpy(st)
+        sim.predict(0.0, out=False)
+        A = args.merger_active
+        act = torch.as_tensor(np.linspace(0, n - 1, A).astype(np.int32), device=dev)
+        o = torch.empty((10, A), dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        nb.nb_evaluate(sim.ctx, 0, act[:1024], 1024, o)   # warm-up
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        nb.nb_evaluate(sim.ctx, 0, act, A, o)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        sec = ev0.elapsed_time(ev1) * 1e-3
+        sim.close()
+        out[prec] = {"interactions_per_s": A * (n - 1) / sec, "seconds": sec,
+                     "gflops_79": A * (n - 1) / sec * FLOPS_PER_INTERACTION / 1e9}
+    print(json.dumps(out))
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -413,14 +570,26 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-interactions", type=float, default=5e8)
     ap.add_argument("--only-fp64", action="store_true", help="headline run only (profiling)")
-    ap.add_argument("--case", choices=["run", "eval"], default="run")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default plan table")
+    ap.add_argument("--slice", type=float, default=SLICE,
+                    help="N-body time per step (a power of two dividing 0.25); shorter for profiling")
+    ap.add_argument("--case", choices=["run", "eval", "batched", "config3", "merger"], default="run")
+    ap.add_argument("--clusters", type=int, default=512)
+    ap.add_argument("--t-warm", type=float, default=1.0 / 256)
+    ap.add_argument("--t-run", type=float, default=1.0 / 64)
+    ap.add_argument("--c3-active", type=int, default=65536)
+    ap.add_argument("--c3-full-fp64", action="store_true")
+    ap.add_argument("--c3-run-t", type=float, default=0.0)
+    ap.add_argument("--c3-run-precisions", default="ex")
+    ap.add_argument("--merger-active", type=int, default=65536)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "ex", "fp32"])
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--active", type=int, default=N)
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args()
-    if args.case == "eval":
-        eval_case(args)
+    if args.case != "run":
+        {"eval": eval_case, "batched": batched_case, "config3": config3_case,
+         "merger": merger_case}[args.case](args)
         return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()

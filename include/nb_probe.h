@@ -18,7 +18,11 @@ extern "C" {
 /*
  * nb_probe_fma_peak -- run a kernel of independent FMA chains (8 per thread,
  * every SM filled) on the current device and time it with CUDA events.
- *   precision   : NB_FP64 (DFMA) or NB_FP32 (FFMA); others -> NB_EINVAL
+ *   precision   : NB_FP64 (DFMA) or NB_FP32 (FFMA), or 3: an FP64 stream of
+ *                 16 DFMA : 6 DMUL : 5 DADD per chain (the fused : non-fused
+ *                 mix of the FP64 pair evaluation), reported as 2 x its
+ *                 instruction rate so it compares with the DFMA figure;
+ *                 others -> NB_EINVAL
  *   iters       : FMA iterations per chain (>= 1), e.g. 4096
  *   stream      : cudaStream_t (NULL = legacy default)
  *   flops_per_s : HOST out, 2 flops per FMA
@@ -28,6 +32,18 @@ extern "C" {
  */
 nb_status nb_probe_fma_peak(int32_t precision, int64_t iters, void *stream, double *flops_per_s,
                             double *seconds);
+
+/*
+ * nb_selftest_wait_timeout -- failure-detection self-test of the bounded
+ * device-side waits the evaluation kernel uses on its TMA pipeline: one CTA
+ * waits on an mbarrier whose byte count nothing will ever satisfy.  The wait
+ * must give up after budget_seconds (0 < budget <= 2), record the timeout in
+ * a device error word and let the kernel finish; the call then returns
+ * NB_ETIMEOUT (the expected answer).  NB_OK would mean the wait did not give
+ * up.  Synchronises `stream`; allocates a 4-byte device word.  Errors:
+ * NB_EINVAL (budget), NB_ENOMEM, NB_ECUDA.
+ */
+nb_status nb_selftest_wait_timeout(double budget_seconds, void *stream);
 
 #ifdef __cplusplus
 }

@@ -39,15 +39,21 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files if os.path.exists(f))
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
+def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None,
+          out_dir: str | None = None, defines: dict | None = None) -> str:
+    """Compile libnb.so.  out_dir / defines build a variant elsewhere (e.g. a
+    debug or tuning build: defines={"NB_EVAL_MIN_BLOCKS": 5})."""
+    out = out_dir or OUT
+    lib = os.path.join(out, "libnb.so")
+    os.makedirs(out, exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    extra += [f"-D{k}={v}" for k, v in (defines or {}).items()]
 
     def compile_one(src: str) -> tuple[str, str]:
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
+        obj = os.path.join(out, src.replace(".cu", ".o"))
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -59,13 +65,13 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     if verbose_ptxas:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

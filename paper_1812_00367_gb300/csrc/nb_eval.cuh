@@ -12,7 +12,8 @@
 // with the large alpha terms cancelling inside each pair before it is summed
 // (that keeps the FP32 path within its bound on strongly cancelling sums).
 // Every per-pair operation is a multiply, an add or a fused multiply-add:
-// 54 FP64 instructions per pair on the FP64 path.
+// 53 FP64 instructions per pair on the FP64 path (one exact doubling is done
+// on the integer pipe).
 //
 // Work decomposition: a work item is (cluster, i-tile, j-range).  An i-tile
 // holds kTPB / gl active particles; gl lanes of a warp share one i and take
@@ -77,7 +78,7 @@ struct Prec<NB_FP64> {
         const double ze = w * y2;
         const double al3 = 3.0 * al;
         const double be3 = 3.0 * fma(al, al, ze);  // 3 beta
-        const double al6 = al3 + al3;
+        const double al6 = twice_int(al3);          // exact doubling, integer pipe
         const double w1x = fma(-al3, rx, vx), w1y = fma(-al3, ry, vy), w1z = fma(-al3, rz, vz);
         const double w2x = fma(-be3, rx, fma(-al6, w1x, ax));
         const double w2y = fma(-be3, ry, fma(-al6, w1y, ay));
@@ -205,8 +206,11 @@ struct Prec<NB_FP32> {
     struct I {
         float xh[3], xl[3], vh[3], vl[3], a[3];
     };
+    // Two FP32 levels: per-tile sums (64 pairs) are added into chunk sums,
+    // which are promoted to FP64 every kFp32FlushTiles tiles.
     struct Acc {
         float a[3], j[3], s[3], p;
+        float ca[3], cj[3], cs[3], cp;
     };
     static __device__ __forceinline__ I load_i(const J *jarr, int64_t k) {
         const J e = jarr[k];
@@ -220,8 +224,8 @@ struct Prec<NB_FP32> {
     }
     static __device__ __forceinline__ void zero(Acc &c) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = 0.f;
-        c.p = 0.f;
+        for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = c.ca[k] = c.cj[k] = c.cs[k] = 0.f;
+        c.p = c.cp = 0.f;
     }
     static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self, double,
                                                     float eps2, Acc &c) {
@@ -240,6 +244,8 @@ struct Prec<NB_FP32> {
         m = self ? 0.f : m;
         float y;
         asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+        const float hr2 = 0.5f * r2;             // one Newton step on the SFU value
+        y = y * fmaf(-hr2 * y, y, 1.5f);
         const float y2 = y * y;
         const float my = m * y;
         const float q = my * y2;
@@ -259,15 +265,26 @@ struct Prec<NB_FP32> {
         c.j[0] = fmaf(q, w1x, c.j[0]); c.j[1] = fmaf(q, w1y, c.j[1]); c.j[2] = fmaf(q, w1z, c.j[2]);
         c.s[0] = fmaf(q, w2x, c.s[0]); c.s[1] = fmaf(q, w2y, c.s[1]); c.s[2] = fmaf(q, w2z, c.s[2]);
     }
-    // Promote the FP32 chunk sums into the FP64 totals and restart them.
-    static __device__ __forceinline__ void flush(Acc &c, double *t64) {
+    // End of a tile: add the tile sums into the chunk sums.
+    static __device__ __forceinline__ void tile_done(Acc &c) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            t64[k] += (double)c.a[k];
-            t64[3 + k] += (double)c.j[k];
-            t64[6 + k] += (double)c.s[k];
+            c.ca[k] += c.a[k]; c.cj[k] += c.j[k]; c.cs[k] += c.s[k];
+            c.a[k] = c.j[k] = c.s[k] = 0.f;
         }
-        t64[9] += (double)c.p;
+        c.cp += c.p;
+        c.p = 0.f;
+    }
+    // Promote the FP32 chunk sums into the FP64 totals and restart them.
+    static __device__ __forceinline__ void flush(Acc &c, double *t64) {
+        tile_done(c);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            t64[k] += (double)c.ca[k];
+            t64[3 + k] += (double)c.cj[k];
+            t64[6 + k] += (double)c.cs[k];
+        }
+        t64[9] += (double)c.cp;
         zero(c);
     }
     static __device__ __forceinline__ void finish(Acc &c, double *t64, double o[10]) {
@@ -333,7 +350,7 @@ __device__ __forceinline__ int64_t next_item_of(const EvalLaunch &L, const Dev &
 }
 
 template <int P, int MODE>
-__global__ void __launch_bounds__(kTPB, 4) k_eval(const Dev d, const EvalLaunch L) {
+__global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, const EvalLaunch L) {
     using T = Prec<P>;
     using J = typename T::J;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -439,12 +456,13 @@ __global__ void __launch_bounds__(kTPB, 4) k_eval(const Dev d, const EvalLaunch 
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact(me, tl[k], jbase + k == ji, eps2, eps2f, acc, eps2ff);
                 } else {
-#pragma unroll 2
+#pragma unroll kEvalUnroll
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact(me, tl[k], jbase + k == ji, eps2, eps2f, acc);
                 }
                 if constexpr (P == NB_FP32) {
                     if ((tt - tb + 1) % kFp32FlushTiles == 0) T::flush(acc, t64);
+                    else T::tile_done(acc);
                 }
             }
             if (!ok) S.fail = 1;

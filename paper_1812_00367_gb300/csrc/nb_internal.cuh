@@ -14,7 +14,17 @@ namespace nb {
 // ---------------------------------------------------------------- constants
 constexpr int kTPB = 128;      // threads per evaluation CTA (4 warps)
 constexpr int kTJ = 64;        // j-particles per shared-memory tile
-constexpr int kStages = 4;     // TMA pipeline depth
+#ifndef NB_EVAL_STAGES
+#define NB_EVAL_STAGES 4
+#endif
+#ifndef NB_EVAL_MIN_BLOCKS
+#define NB_EVAL_MIN_BLOCKS 4  // resident evaluation CTAs per SM the compiler must allow
+#endif
+#ifndef NB_EVAL_UNROLL
+#define NB_EVAL_UNROLL 2      // j-loop unrolling of the FP64 / FP32 evaluation
+#endif
+constexpr int kStages = NB_EVAL_STAGES;  // TMA pipeline depth
+constexpr int kEvalUnroll = NB_EVAL_UNROLL;
 constexpr int kChunk = 2048;   // particles per select / predict chunk
 constexpr int kSelTPB = 256;   // threads per select / predict CTA
 constexpr int kPlanTPB = 1024; // threads of the single planning CTA
@@ -187,6 +197,17 @@ __device__ __forceinline__ double rsqrt_f64(double r2) {
     return fma(t, p, y0);
 }
 
+// 2x by adding one to the exponent field on the integer pipe (exact for
+// normal x whose double does not overflow).  Zero, subnormal, infinite and NaN
+// inputs are returned unchanged (a subnormal is then off by a factor two, at
+// the 1e-308 level; a NaN stays NaN).
+__device__ __forceinline__ double twice_int(double x) {
+    const int hi = __double2hiint(x);
+    const int ex = hi & 0x7ff00000;
+    const bool ok = ex != 0 && ex < 0x7fe00000;
+    return __hiloint2double(ok ? hi + 0x00100000 : hi, __double2loint(x));
+}
+
 // ------------------------------------------------------- float-float (EX)
 // A value is hi + lo with |lo| <= ulp(hi)/2 (Dekker 1971; Knuth TAOCP 2;
 // Hida, Li & Bailey 2001 for the double-double algorithms, here on floats).
@@ -321,12 +342,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait: false after kWaitBudgetNs without completion.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long budget_ns = kWaitBudgetNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > kWaitBudgetNs) return false;
+        if (globaltimer_ns() - t0 > budget_ns) return false;
     }
 }
 

@@ -7,14 +7,39 @@ namespace {
 constexpr int kChains = 8;
 constexpr int kThreads = 256;
 
-template <typename T>
+// Multiplies and adds that the compiler may not contract into FMAs.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+// MIX = false: one FMA per chain per iteration.  MIX = true: per chain and
+// iteration 16 FMA, 6 multiplies and 5 adds (the 32 : 22 fused : non-fused
+// ratio of the FP64 pair evaluation), 27 instructions.
+template <typename T, bool MIX>
 __global__ void __launch_bounds__(kThreads) k_fma(T *sink, int64_t iters, T b, T c) {
     T acc[kChains];
 #pragma unroll
     for (int k = 0; k < kChains; ++k) acc[k] = (T)(threadIdx.x + k);
     for (int64_t it = 0; it < iters; ++it) {
+        if constexpr (!MIX) {
 #pragma unroll
-        for (int k = 0; k < kChains; ++k) acc[k] = fma(acc[k], b, c);
+            for (int k = 0; k < kChains; ++k) acc[k] = fma(acc[k], b, c);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+#pragma unroll
+                for (int k = 0; k < kChains; ++k) acc[k] = fma(acc[k], b, c);
+                if (r < 6) {
+#pragma unroll
+                    for (int k = 0; k < kChains; ++k) acc[k] = mul_rn(acc[k], b);
+                }
+                if (r < 5) {
+#pragma unroll
+                    for (int k = 0; k < kChains; ++k) acc[k] = add_rn(acc[k], c);
+                }
+            }
+        }
     }
     T s = 0;
 #pragma unroll
@@ -22,12 +47,12 @@ __global__ void __launch_bounds__(kThreads) k_fma(T *sink, int64_t iters, T b, T
     sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-template <typename T>
+template <typename T, bool MIX>
 nb_status run(int64_t iters, cudaStream_t st, double *fps, double *sec) {
     int dev = 0, sms = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return NB_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NB_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fma<T>, kThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fma<T, MIX>, kThreads, 0) != cudaSuccess)
         return NB_ECUDA;
     const int blocks = sms * (occ > 0 ? occ : 1);
     T *sink = nullptr;
@@ -36,9 +61,9 @@ nb_status run(int64_t iters, cudaStream_t st, double *fps, double *sec) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     // b slightly below 1 keeps the chains finite; c keeps them from decaying to 0
-    k_fma<T><<<blocks, kThreads, 0, st>>>(sink, iters / 8 + 1, (T)0.999999, (T)1e-3);  // warm-up
+    k_fma<T, MIX><<<blocks, kThreads, 0, st>>>(sink, iters / 8 + 1, (T)0.999999, (T)1e-3);  // warm-up
     cudaEventRecord(e0, st);
-    k_fma<T><<<blocks, kThreads, 0, st>>>(sink, iters, (T)0.999999, (T)1e-3);
+    k_fma<T, MIX><<<blocks, kThreads, 0, st>>>(sink, iters, (T)0.999999, (T)1e-3);
     cudaEventRecord(e1, st);
     cudaError_t e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -47,7 +72,8 @@ nb_status run(int64_t iters, cudaStream_t st, double *fps, double *sec) {
     cudaEventDestroy(e1);
     cudaFree(sink);
     if (e != cudaSuccess || ms <= 0.f) return NB_ECUDA;
-    const double flops = 2.0 * kChains * (double)iters * (double)blocks * kThreads;
+    // instructions x 2: an FMA-equivalent rate, comparable across MIX
+    const double flops = 2.0 * kChains * (double)iters * (double)blocks * kThreads * (MIX ? 27.0 : 1.0);
     if (fps) *fps = flops / (ms * 1e-3);
     if (sec) *sec = ms * 1e-3;
     return NB_OK;
@@ -58,7 +84,49 @@ extern "C" nb_status nb_probe_fma_peak(int32_t precision, int64_t iters, void *s
                                        double *flops_per_s, double *seconds) {
     if (iters < 1) return NB_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (precision == NB_FP64) return run<double>(iters, st, flops_per_s, seconds);
-    if (precision == NB_FP32) return run<float>(iters, st, flops_per_s, seconds);
+    if (precision == NB_FP64) return run<double, false>(iters, st, flops_per_s, seconds);
+    if (precision == NB_FP32) return run<float, false>(iters, st, flops_per_s, seconds);
+    if (precision == 3) return run<double, true>(iters, st, flops_per_s, seconds);
     return NB_EINVAL;
+}
+
+// ------------------------------------------------------------------------
+// Failure-detection self-test: the bounded mbarrier wait of the evaluation
+// kernel, run against a barrier whose transaction count nothing will ever
+// satisfy.  The wait gives up after its budget, records the timeout bit in a
+// device word, and the kernel returns normally: no fault, no hang, the
+// context stays usable.
+#include "nb_internal.cuh"
+
+namespace {
+__global__ void k_selftest_wait(unsigned long long budget_ns, uint32_t *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        nb::mbar_init(&bar, 1);
+        nb::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) nb::mbar_expect_tx(&bar, 16);  // 16 bytes that never arrive
+    __syncthreads();
+    const bool ok = nb::mbar_wait_bounded(&bar, 0, budget_ns);
+    if (!ok && threadIdx.x == 0) atomicOr(err, nb::kErrTimeout);
+}
+}  // namespace
+
+extern "C" nb_status nb_selftest_wait_timeout(double budget_seconds, void *stream) {
+    if (!(budget_seconds > 0.0) || budget_seconds > 2.0) return NB_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t *d_err = nullptr;
+    if (cudaMalloc(&d_err, sizeof(uint32_t)) != cudaSuccess) return NB_ENOMEM;
+    uint32_t h_err = 0;
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<1, 64, 0, st>>>((unsigned long long)(budget_seconds * 1e9), d_err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_err);
+    if (e != cudaSuccess) return NB_ECUDA;
+    return (h_err & nb::kErrTimeout) ? NB_ETIMEOUT : NB_OK;
 }

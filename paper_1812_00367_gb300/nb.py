@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
             "nb_status_string": ([C.c_int], C.c_char_p),
             "nb_free": ([vp], None),
             "nb_probe_fma_peak": ([i32, i64, vp, pd, pd], C.c_int),
+            "nb_selftest_wait_timeout": ([d, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -312,3 +313,8 @@ class Simulation:
             a = np.asarray(st[f], dtype=np.float64)
             host[f] = np.ascontiguousarray(a.T if f in VECTOR_FIELDS else a)
         nb_set_state(self.ctx, host_state(host))
+
+
+def nb_selftest_wait_timeout(budget_seconds: float, stream=None) -> int:
+    """Returns the raw status: NB_ETIMEOUT (6) is the expected answer."""
+    return int(load().nb_selftest_wait_timeout(float(budget_seconds), _stream_handle(stream)))
