@@ -375,11 +375,21 @@ def batched_case(args):
     for prec in ("fp64", "ex"):
         sim = nb.Simulation(batch.m, batch.x, batch.v, eps=EPS, eta=ETA, dt_min=DT_MIN,
                             dt_max=DT_MAX, precision=prec, offsets=batch.offsets)
-        e0 = [sum(sim.energy(0.0, c)[:2]) for c in range(args.clusters)]
+        if args.batched_target > 0:   # one split target for every active-set size
+            import tempfile
+            path = os.path.join(tempfile.mkdtemp(), "table.txt")
+            with open(path, "w") as f:
+                f.write(f"nbtune {nb.PRECISIONS[prec]} 0\n")
+                for b in range(32):
+                    gl = 32 if b < 6 else (8 if b < 10 else (2 if b < 12 else 1))
+                    f.write(f"{gl} {args.batched_target}\n")
+            sim.autotune(path)
+            out["batched_target"] = args.batched_target
+        e0 = list(sim.energy_all(0.0)[:, :2].sum(axis=1))
         sim.run(args.t_warm)
         steps, inter, sec = _timed_run(sim, torch, dev, args.t_warm + args.t_run)
         t1 = args.t_warm + args.t_run
-        e1 = [sum(sim.energy(t1, c)[:2]) for c in range(args.clusters)]
+        e1 = list(sim.energy_all(t1)[:, :2].sum(axis=1))
         drift = [abs(b - a) / abs(a) / t1 for a, b in zip(e0, e1)]
         out[prec] = {"interactions_per_s": inter / sec, "seconds": sec, "cluster_block_steps": steps,
                      "interactions": inter, "energy_drift_per_time_max": max(drift),
@@ -575,6 +585,8 @@ def main():
                     help="N-body time per step (a power of two dividing 0.25); shorter for profiling")
     ap.add_argument("--case", choices=["run", "eval", "batched", "config3", "merger"], default="run")
     ap.add_argument("--clusters", type=int, default=512)
+    ap.add_argument("--batched-target", type=int, default=0,
+                    help="split target per cluster for --case batched (0: library default)")
     ap.add_argument("--t-warm", type=float, default=1.0 / 256)
     ap.add_argument("--t-run", type=float, default=1.0 / 64)
     ap.add_argument("--c3-active", type=int, default=65536)

@@ -204,6 +204,14 @@ nb_status nb_run(nb_ctx *ctx, double t_end, int64_t max_block_steps, int64_t *bl
 nb_status nb_energy(nb_ctx *ctx, int32_t cluster, double t, double *ekin, double *epot,
                     double P[3], double L[3]);
 
+/*
+ * nb_energy_all -- the diagnostics of nb_energy for every cluster at once
+ * (one potential evaluation of the whole batch at common time t).
+ *   out : HOST double [n_clusters][8]: E_kin, E_pot, P[3], L[3] per cluster
+ * Synchronises.  Errors: NB_EINVAL, NB_ECUDA.
+ */
+nb_status nb_energy_all(nb_ctx *ctx, double t, double *out);
+
 /* nb_get_state / nb_set_state -- copy the whole particle state out of / into
  * the context's buffers.  dst / src pointers may be HOST or DEVICE (any mix).
  * Synchronises.  Used for checkpoint / resume and host-side I/O. */

@@ -22,6 +22,8 @@ extern "C" {
  *                 16 DFMA : 6 DMUL : 5 DADD per chain (the fused : non-fused
  *                 mix of the FP64 pair evaluation), reported as 2 x its
  *                 instruction rate so it compares with the DFMA figure;
+ *                 4: the same stream with its multiplies and adds issued as
+ *                 FMAs (x*b - 0, x*1 + c); 5: DADD only; 6: DMUL only;
  *                 others -> NB_EINVAL
  *   iters       : FMA iterations per chain (>= 1), e.g. 4096
  *   stream      : cudaStream_t (NULL = legacy default)

@@ -53,6 +53,7 @@ struct nb_ctx {
     int64_t n = 0;
     int32_t nc = 1;
     std::vector<int64_t> h_offsets, h_jofs;
+    std::vector<int32_t> h_chunk0;       // first chunk of each cluster [nc + 1]
     int64_t max_cluster = 0;
     Dev d{};
     Dev d_pot{};  // FP64 view for energy
@@ -120,8 +121,13 @@ void default_table(nb_ctx *ctx) {
         else if (A < 4096) gl = 2;
         // per-cluster split target: a few waves of the grid for one cluster,
         // shared out when many clusters advance together
-        const int64_t tgt = std::max<int64_t>(1, 8LL * ctx->grid_eval / ctx->nc);
-        ctx->table[b] = PlanEntry{gl, (int32_t)std::min<int64_t>(tgt, ctx->cap_items / (2LL * ctx->nc))};
+        // (a batch keeps the grid busy with many clusters; its per-cluster
+        // target shrinks with the fourth root of the cluster count: for 512
+        // clusters the measured FP64 rate rose from 7.2e9 at 9 items per
+        // cluster to 1.10e10 at 215 and 1.12e10 at 1216)
+        const int64_t tgt = std::max<int64_t>(
+            1, (int64_t)(8.0 * ctx->grid_eval / std::pow((double)ctx->nc, 0.25)));
+        ctx->table[b] = PlanEntry{gl, (int32_t)tgt};
     }
 }
 
@@ -213,7 +219,9 @@ void plan_direct(const nb_ctx *ctx, int cluster, int32_t n_active, int &gl, int 
     const int64_t ncl = ctx->h_offsets[cluster + 1] - ctx->h_offsets[cluster];
     const int64_t ntj = cdiv(ncl, kTJ);
     int64_t S = choose_split(tiles, ntj, e.target_items, ctx->grid_eval);
-    if (S > 1 && (int64_t)tiles * S > ctx->cap_items) S = std::max<int64_t>(1, ctx->cap_items / tiles);
+    const int64_t per_item = 10LL * (kTPB / gl);  // partial doubles per item
+    if (S > 1 && (int64_t)tiles * S * per_item > ctx->d.partial_cap)
+        S = std::max<int64_t>(1, ctx->d.partial_cap / (per_item * tiles));
     split = (int)S;
 }
 
@@ -348,6 +356,7 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
         ctx->h_jofs[c + 1] = ctx->h_jofs[c] + cdiv(ncl, kTJ) * kTJ;
     }
     cluster_chunk0[n_clusters] = (int32_t)chunk_cluster.size();
+    ctx->h_chunk0 = cluster_chunk0;
     const int n_chunks = (int)chunk_cluster.size();
     const int64_t nj = ctx->h_jofs[n_clusters];
 
@@ -363,13 +372,23 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     d.eta_init = p->eta_init;
     d.dt_min = p->dt_min;
     d.dt_max = p->dt_max;
+    d.neg_one = -1.0;
+    d.neg_zero = -0.0;
 
     const int occ = std::max(1, eval_occupancy(p->precision, kModeStep));
     ctx->grid_eval = occ * ctx->sm_count;
     ctx->grid_pot = std::max(1, eval_occupancy(NB_FP64, kModePot)) * ctx->sm_count;
     d.grid_eval = ctx->grid_eval;
-    ctx->cap_items = 32LL * ctx->grid_eval;
-    d.partial_items = ctx->cap_items;
+    // split partial sums, in full-width items (10 x 128 doubles): 32 waves of
+    // the grid for one cluster; a batch gets room for every cluster at twice
+    // its default target (at most 2 GB), so the planner's fall-back to
+    // unsplit work stays an exception
+    {
+        const double batch = 2.0 * n_clusters * (8.0 * ctx->grid_eval / std::pow((double)n_clusters, 0.25));
+        const double two_gb_items = 2.0e9 / (10.0 * kTPB * sizeof(double));
+        ctx->cap_items = (int64_t)std::max(32.0 * ctx->grid_eval, std::min(batch, two_gb_items));
+    }
+    d.partial_cap = ctx->cap_items * 10 * kTPB;  // doubles
 
     int64_t *d_offs = nullptr, *d_jofs = nullptr, *d_cb = nullptr, *d_ce = nullptr;
     int32_t *d_ccl = nullptr, *d_cc0 = nullptr;
@@ -620,6 +639,29 @@ nb_status nb_energy(nb_ctx *ctx, int32_t cluster, double t, double *ekin, double
     if (epot) *epot = acc[1];
     if (P) for (int q = 0; q < 3; ++q) P[q] = acc[2 + q];
     if (L) for (int q = 0; q < 3; ++q) L[q] = acc[5 + q];
+    return check_device_error(ctx);
+}
+
+nb_status nb_energy_all(nb_ctx *ctx, double t, double *out) {
+    if (!ctx) return fail(nullptr, NB_EINVAL, "nb_energy_all: NULL context");
+    if (!out || !std::isfinite(t)) return fail(ctx, NB_EINVAL, "nb_energy_all: NULL out or bad t");
+    NB_CU(ctx, launch_predict(ctx->d, 1, 1, t, ctx->stream));
+    NB_CU(ctx, launch_plan_ex(ctx->d_pot, 1, 0, ctx->stream));
+    EvalLaunch Lz{};
+    Lz.identity = 1;
+    NB_CU(ctx, launch_eval(ctx->d_pot, kModePot, Lz, ctx->grid_pot, ctx->stream));
+    NB_CU(ctx, launch_energy(ctx->d, 0, ctx->n, 0, ctx->stream));
+    std::vector<double> part((size_t)ctx->d.n_chunks * 8);
+    NB_CU(ctx, cudaMemcpyAsync(part.data(), ctx->d.energy_part, part.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    NB_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    // chunks never straddle clusters and are numbered cluster by cluster
+    for (int c = 0; c < ctx->nc; ++c) {
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = ctx->h_chunk0[c]; k < ctx->h_chunk0[c + 1]; ++k)
+            for (int q = 0; q < 8; ++q) acc[q] += part[(size_t)k * 8 + q];
+        for (int q = 0; q < 8; ++q) out[(size_t)c * 8 + q] = acc[q];
+    }
     return check_device_error(ctx);
 }
 

@@ -40,10 +40,30 @@ struct Prec<NB_FP64> {
     using J = J64;
     struct I {
         double x[3], v[3], a[3];
+        double m1, nz;  // -1.0, -0.0 from kernel parameters (see Dev)
     };
     struct Acc {
         double a[3], j[3], s[3], p;
     };
+    static __device__ __forceinline__ void prepare(I &i, const Dev &d) {
+        i.m1 = d.neg_one;
+        i.nz = d.neg_zero;
+    }
+    // product and difference; as FMAs with run-time -0.0 / -1.0 when
+    // NB_FP64_ALL_FMA (same IEEE results: a*b + (-0) == a*b, b*(-1) + a == a - b)
+    static __device__ __forceinline__ double fma_rt(double a, double b, double c) {
+        double r;
+        asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(b), "d"(c));
+        return r;
+    }
+    static __device__ __forceinline__ double mul(const I &i, double a, double b) {
+        if constexpr (NB_FP64_ALL_FMA) return fma_rt(a, b, i.nz);
+        else return a * b;
+    }
+    static __device__ __forceinline__ double sub(const I &i, double a, double b) {
+        if constexpr (NB_FP64_ALL_FMA) return fma_rt(b, i.m1, a);
+        else return a - b;
+    }
     static __device__ __forceinline__ I load_i(const J *jarr, int64_t k) {
         const J e = jarr[k];
         I r;
@@ -60,24 +80,23 @@ struct Prec<NB_FP64> {
     static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self,
                                                     double eps2, float, Acc &c) {
         const double2 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3], q4 = jj.q[4];
-        const double rx = q0.x - i.x[0], ry = q0.y - i.x[1], rz = q1.x - i.x[2];
-        const double vx = q2.x - i.v[0], vy = q2.y - i.v[1], vz = q3.x - i.v[2];
-        const double ax = q3.y - i.a[0], ay = q4.x - i.a[1], az = q4.y - i.a[2];
+        const double rx = sub(i, q0.x, i.x[0]), ry = sub(i, q0.y, i.x[1]), rz = sub(i, q1.x, i.x[2]);
+        const double vx = sub(i, q2.x, i.v[0]), vy = sub(i, q2.y, i.v[1]), vz = sub(i, q3.x, i.v[2]);
+        const double ax = sub(i, q3.y, i.a[0]), ay = sub(i, q4.x, i.a[1]), az = sub(i, q4.y, i.a[2]);
         double r2 = fma(rx, rx, fma(ry, ry, fma(rz, rz, eps2)));
         double m = q1.y;
         r2 = self ? 1.0 : r2;  // selects, not FP64 arithmetic
         m = self ? 0.0 : m;
-        const double y = rsqrt_f64(r2);
-        const double y2 = y * y;
-        const double my = m * y;
-        const double q = my * y2;
-        c.p += my;
-        const double rv = fma(rx, vx, fma(ry, vy, rz * vz));
-        const double w = fma(vx, vx, fma(vy, vy, fma(vz, vz, fma(rx, ax, fma(ry, ay, rz * az)))));
-        const double al = rv * y2;
-        const double ze = w * y2;
-        const double al3 = 3.0 * al;
-        const double be3 = 3.0 * fma(al, al, ze);  // 3 beta
+        const double y = NB_FP64_ALL_FMA ? rsqrt_f64_fma(r2, i.nz) : rsqrt_f64(r2);
+        const double y2 = mul(i, y, y);
+        c.p = fma(m, y, c.p);                      // potential: sum m y
+        const double q = mul(i, mul(i, m, y2), y); // m y^3
+        const double rv = fma(rx, vx, fma(ry, vy, mul(i, rz, vz)));
+        const double w = fma(vx, vx, fma(vy, vy, fma(vz, vz, fma(rx, ax, fma(ry, ay, mul(i, rz, az))))));
+        const double al = mul(i, rv, y2);
+        const double ze = mul(i, w, y2);
+        const double al3 = mul(i, 3.0, al);
+        const double be3 = mul(i, 3.0, fma(al, al, ze));  // 3 beta
         const double al6 = twice_int(al3);          // exact doubling, integer pipe
         const double w1x = fma(-al3, rx, vx), w1y = fma(-al3, ry, vy), w1z = fma(-al3, rz, vz);
         const double w2x = fma(-be3, rx, fma(-al6, w1x, ax));
@@ -420,7 +439,8 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
             }
         }
         const int64_t ji = gi - off;
-        const typename T::I me = T::load_i(jc, ji);
+        typename T::I me = T::load_i(jc, ji);
+        if constexpr (P == NB_FP64) T::prepare(me, d);
         typename T::Acc acc;
         T::zero(acc);
         double t64[10];
@@ -501,10 +521,10 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
             item = next_item_of<P>(L, d, S, item);
             continue;
         }
-        double *part = d.partial + (pslot0 + local) * (int64_t)(10 * kTPB);
+        double *part = d.partial + pslot0 + local * (int64_t)(10 * Ti);
         if (jsub == 0) {
 #pragma unroll
-            for (int q = 0; q < 10; ++q) part[q * kTPB + ilane] = o[q];
+            for (int q = 0; q < 10; ++q) part[q * Ti + ilane] = o[q];
         }
         __threadfence();
         __syncthreads();
@@ -523,14 +543,14 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
             const int nv = min(Ti, A - tile * Ti);     // valid i in this tile
             const int npair = nv * 10;
             const int R = max(1, kTPB / npair);
-            const double *base = d.partial + (pslot0 + (int64_t)tile * split) * (10 * kTPB);
+            const double *base = d.partial + pslot0 + (int64_t)tile * split * (10 * Ti);
             for (int w = tid; w < npair * R; w += kTPB) {
                 const int p = w % npair, r = w / npair;
                 const int q = p / nv, il = p % nv;
                 const int s0 = (int)((int64_t)split * r / R), s1 = (int)((int64_t)split * (r + 1) / R);
                 double acc = 0.0;
 #pragma unroll 4
-                for (int sp = s0; sp < s1; ++sp) acc += __ldcg(base + (int64_t)sp * (10 * kTPB) + q * kTPB + il);
+                for (int sp = s0; sp < s1; ++sp) acc += __ldcg(base + (int64_t)sp * (10 * Ti) + q * Ti + il);
                 S.red[r * npair + p] = acc;
             }
             __syncthreads();

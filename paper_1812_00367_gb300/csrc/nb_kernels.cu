@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan(const Dev d, int mode_init, i
     for (int fallback = 0; fallback < 2; ++fallback) {
         long long carry_items = 0, carry_tiles = 0, carry_slots = 0;
         double inter = 0.0, busy = 0.0;
-        for (int base = 0; base < d.n_clusters; base += kPlanTPB) {
+        for (int base = 0; base < d.n_clusters; base += (int)blockDim.x) {
             const int c = base + tid;
             ClusterPlan pl{1, 1, 0, 0, 0, 0, 0};
             long long items = 0, tiles = 0;
@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan(const Dev d, int mode_init, i
                     my_inter = (double)A * (double)(ncl - 1);
                 }
             }
-            const long long sitems = pl.split > 1 ? items : 0;
+            // partial sums: 10 doubles per i of every item of a split cluster
+            const long long sitems = pl.split > 1 ? items * 10 * (kTPB / pl.gl) : 0;
             const long long ii = block_scan_incl(items, s_l);
             const long long it = block_scan_incl(tiles, s_l);
             const long long is = block_scan_incl(sitems, s_l);
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan(const Dev d, int mode_init, i
             pl.pslot0 = carry_slots + is - sitems;
             if (c < d.n_clusters) d.plan[c] = pl;
             // the last thread holds the inclusive totals
-            if (tid == kPlanTPB - 1) {
+            if (tid == (int)blockDim.x - 1) {
                 s_l[0] = ii;
                 s_l[1] = it;
                 s_l[2] = is;
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan(const Dev d, int mode_init, i
             busy += block_sum_d(pl.active > 0 ? 1.0 : 0.0, s_d);
         }
         // the split items' partial sums must fit the scratch (uniform decision)
-        if (!fallback && carry_slots > d.partial_items) continue;
+        if (!fallback && carry_slots > d.partial_cap) continue;
         if (tid == 0) {
             *d.n_items = carry_items;
             *d.item_ctr = 0ull;
@@ -375,7 +376,10 @@ cudaError_t launch_select_compact(const Dev &d, double, cudaStream_t st) {
     return cudaGetLastError();
 }
 cudaError_t launch_plan_ex(const Dev &d, int mode_init, int count, cudaStream_t st) {
-    k_plan<<<1, kPlanTPB, 0, st>>>(d, mode_init, count);
+    // a power of two >= the cluster count (the scans assume it), 32..1024
+    int threads = 32;
+    while (threads < d.n_clusters && threads < kPlanTPB) threads *= 2;
+    k_plan<<<1, threads, 0, st>>>(d, mode_init, count);
     return cudaGetLastError();
 }
 cudaError_t launch_unpack64(const Dev &d, double *out, cudaStream_t st) {

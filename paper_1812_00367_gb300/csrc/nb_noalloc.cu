@@ -136,8 +136,10 @@ extern "C" nb_status nb_evaluate_noalloc(const double *jpred, int64_t n, double 
     const int tiles = (int)cdiv(n_active, kTPB / gl);
     const int64_t ntj = cdiv(n, kTJ);
     int64_t split = choose_split(tiles, ntj, 8LL * slot.grid, slot.grid);
-    if (split > 1 && (int64_t)tiles * split > kNaMaxItems)
-        split = kNaMaxItems / tiles > 1 ? kNaMaxItems / tiles : 1;
+    const int64_t per_item = 10LL * (kTPB / gl);         // partial doubles per item
+    const int64_t cap = kNaMaxItems * 10LL * kTPB;        // arena partial doubles
+    if (split > 1 && (int64_t)tiles * split * per_item > cap)
+        split = cap / (per_item * tiles) > 1 ? cap / (per_item * tiles) : 1;
 
     k_na_prepare<<<(unsigned)cdiv(ntj * kTJ, 256), 256, 0, st>>>(slot.base, jpred, n, ntj * kTJ,
                                                                   tiles);
@@ -154,10 +156,12 @@ extern "C" nb_status nb_evaluate_noalloc(const double *jpred, int64_t n, double 
     d.jarr = slot.base + kNaOffJarr;
     d.jarr64 = reinterpret_cast<J64 *>(slot.base + kNaOffJarr);
     d.partial = reinterpret_cast<double *>(slot.base + kNaOffPart);
-    d.partial_items = kNaMaxItems;
+    d.partial_cap = kNaMaxItems * 10 * kTPB;  // doubles
     d.tile_cnt = reinterpret_cast<int32_t *>(slot.base + kNaOffTile);
     d.err = &aux->err;
     d.eps2 = eps * eps;
+    d.neg_one = -1.0;
+    d.neg_zero = -0.0;
     EvalLaunch L{};
     L.direct = 1;
     L.cluster = 0;

@@ -12,19 +12,42 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+// The same products and sums issued as fused multiply-adds (x*b - 0, x*1 + c)
+// with the constants passed at run time, so no compiler can fold them back.
+__device__ __forceinline__ double fma_ptx(double a, double b, double c) {
+    double r;
+    asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(b), "d"(c));
+    return r;
+}
+__device__ __forceinline__ float fma_ptx(float a, float b, float c) {
+    float r;
+    asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 
-// MIX = false: one FMA per chain per iteration.  MIX = true: per chain and
-// iteration 16 FMA, 6 multiplies and 5 adds (the 32 : 22 fused : non-fused
-// ratio of the FP64 pair evaluation), 27 instructions.
-template <typename T, bool MIX>
-__global__ void __launch_bounds__(kThreads) k_fma(T *sink, int64_t iters, T b, T c) {
+// Instruction streams per chain and iteration (8 independent chains/thread):
+//   kPure: 1 FMA
+//   kMix: 16 FMA + 6 multiplies + 5 adds (the FP64 evaluation's fused :
+//         non-fused ratio), 27 instructions
+//   kMixFma: kMix with the multiplies and adds issued as FMAs
+//   kAdd / kMul: 1 add / 1 multiply
+enum ProbeMode { kPure = 0, kMix = 1, kMixFma = 2, kAdd = 3, kMul = 4 };
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_fma(T *sink, int64_t iters, T b, T c, T one, T nzero) {
     T acc[kChains];
 #pragma unroll
     for (int k = 0; k < kChains; ++k) acc[k] = (T)(threadIdx.x + k);
     for (int64_t it = 0; it < iters; ++it) {
-        if constexpr (!MIX) {
+        if constexpr (MODE == kPure) {
 #pragma unroll
             for (int k = 0; k < kChains; ++k) acc[k] = fma(acc[k], b, c);
+        } else if constexpr (MODE == kAdd) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) acc[k] = add_rn(acc[k], c);
+        } else if constexpr (MODE == kMul) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) acc[k] = mul_rn(acc[k], b);
         } else {
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
@@ -32,11 +55,13 @@ __global__ void __launch_bounds__(kThreads) k_fma(T *sink, int64_t iters, T b, T
                 for (int k = 0; k < kChains; ++k) acc[k] = fma(acc[k], b, c);
                 if (r < 6) {
 #pragma unroll
-                    for (int k = 0; k < kChains; ++k) acc[k] = mul_rn(acc[k], b);
+                    for (int k = 0; k < kChains; ++k)
+                        acc[k] = MODE == kMix ? mul_rn(acc[k], b) : fma_ptx(acc[k], b, nzero);
                 }
                 if (r < 5) {
 #pragma unroll
-                    for (int k = 0; k < kChains; ++k) acc[k] = add_rn(acc[k], c);
+                    for (int k = 0; k < kChains; ++k)
+                        acc[k] = MODE == kMix ? add_rn(acc[k], c) : fma_ptx(acc[k], one, c);
                 }
             }
         }
@@ -47,12 +72,12 @@ __global__ void __launch_bounds__(kThreads) k_fma(T *sink, int64_t iters, T b, T
     sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-template <typename T, bool MIX>
+template <typename T, int MODE>
 nb_status run(int64_t iters, cudaStream_t st, double *fps, double *sec) {
     int dev = 0, sms = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return NB_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NB_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fma<T, MIX>, kThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fma<T, MODE>, kThreads, 0) != cudaSuccess)
         return NB_ECUDA;
     const int blocks = sms * (occ > 0 ? occ : 1);
     T *sink = nullptr;
@@ -61,9 +86,10 @@ nb_status run(int64_t iters, cudaStream_t st, double *fps, double *sec) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     // b slightly below 1 keeps the chains finite; c keeps them from decaying to 0
-    k_fma<T, MIX><<<blocks, kThreads, 0, st>>>(sink, iters / 8 + 1, (T)0.999999, (T)1e-3);  // warm-up
+    const T b = (T)0.999999, c = (T)1e-3, one = (T)1, nzero = -(T)0;
+    k_fma<T, MODE><<<blocks, kThreads, 0, st>>>(sink, iters / 8 + 1, b, c, one, nzero);  // warm-up
     cudaEventRecord(e0, st);
-    k_fma<T, MIX><<<blocks, kThreads, 0, st>>>(sink, iters, (T)0.999999, (T)1e-3);
+    k_fma<T, MODE><<<blocks, kThreads, 0, st>>>(sink, iters, b, c, one, nzero);
     cudaEventRecord(e1, st);
     cudaError_t e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -72,8 +98,9 @@ nb_status run(int64_t iters, cudaStream_t st, double *fps, double *sec) {
     cudaEventDestroy(e1);
     cudaFree(sink);
     if (e != cudaSuccess || ms <= 0.f) return NB_ECUDA;
-    // instructions x 2: an FMA-equivalent rate, comparable across MIX
-    const double flops = 2.0 * kChains * (double)iters * (double)blocks * kThreads * (MIX ? 27.0 : 1.0);
+    // instructions x 2: an FMA-equivalent rate, comparable across modes
+    const double per_iter = (MODE == kMix || MODE == kMixFma) ? 27.0 : 1.0;
+    const double flops = 2.0 * kChains * (double)iters * (double)blocks * kThreads * per_iter;
     if (fps) *fps = flops / (ms * 1e-3);
     if (sec) *sec = ms * 1e-3;
     return NB_OK;
@@ -84,9 +111,15 @@ extern "C" nb_status nb_probe_fma_peak(int32_t precision, int64_t iters, void *s
                                        double *flops_per_s, double *seconds) {
     if (iters < 1) return NB_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (precision == NB_FP64) return run<double, false>(iters, st, flops_per_s, seconds);
-    if (precision == NB_FP32) return run<float, false>(iters, st, flops_per_s, seconds);
-    if (precision == 3) return run<double, true>(iters, st, flops_per_s, seconds);
+    switch (precision) {
+    case NB_FP64: return run<double, kPure>(iters, st, flops_per_s, seconds);
+    case NB_FP32: return run<float, kPure>(iters, st, flops_per_s, seconds);
+    case 3: return run<double, kMix>(iters, st, flops_per_s, seconds);
+    case 4: return run<double, kMixFma>(iters, st, flops_per_s, seconds);
+    case 5: return run<double, kAdd>(iters, st, flops_per_s, seconds);
+    case 6: return run<double, kMul>(iters, st, flops_per_s, seconds);
+    default: break;
+    }
     return NB_EINVAL;
 }
 

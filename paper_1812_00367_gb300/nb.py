@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
             "nb_step": ([vp, pd, C.POINTER(C.c_int32)], C.c_int),
             "nb_run": ([vp, d, i64, C.POINTER(C.c_int64), pd], C.c_int),
             "nb_energy": ([vp, i32, d, pd, pd, pd, pd], C.c_int),
+            "nb_energy_all": ([vp, d, pd], C.c_int),
             "nb_get_state": ([vp, C.POINTER(nb_state)], C.c_int),
             "nb_set_state": ([vp, C.POINTER(nb_state)], C.c_int),
             "nb_get_counters": ([vp, C.POINTER(nb_counters)], C.c_int),
@@ -183,6 +184,13 @@ def nb_energy(ctx, cluster: int, t: float):
     Lm = (C.c_double * 3)()
     _check(load().nb_energy(ctx, int(cluster), float(t), C.byref(ek), C.byref(ep), P, Lm), ctx)
     return ek.value, ep.value, np.array(P[:]), np.array(Lm[:])
+
+
+def nb_energy_all(ctx, n_clusters: int, t: float) -> np.ndarray:
+    """(n_clusters, 8) array: E_kin, E_pot, P[3], L[3] of every cluster."""
+    out = np.zeros((n_clusters, 8))
+    _check(load().nb_energy_all(ctx, float(t), out.ctypes.data_as(C.POINTER(C.c_double))), ctx)
+    return out
 
 
 def nb_get_state(ctx, dst: nb_state):
@@ -290,6 +298,10 @@ class Simulation:
 
     def energy(self, t, cluster=-1):
         return nb_energy(self.ctx, cluster, t)
+
+    def energy_all(self, t):
+        nc = 1 if self.offsets is None else len(self.offsets) - 1
+        return nb_energy_all(self.ctx, nc, t)
 
     def counters(self):
         return nb_get_counters(self.ctx)

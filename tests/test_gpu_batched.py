@@ -161,3 +161,15 @@ def test_argument_errors(nb):
     nb.nb_evaluate(sim.ctx, 0, act, 0, out)           # empty: no-op
     sim.sync()
     sim.close()
+
+
+def test_energy_all_matches_per_cluster(nb):
+    sizes = [200, 900, 411]
+    batch = ic.plummer_batch(sizes=sizes, seed=9)
+    sim = nb.Simulation(batch.m, batch.x, batch.v, eps=1e-2, offsets=batch.offsets)
+    sim.run(1.0 / 64)
+    allc = sim.energy_all(1.0 / 64)
+    for c in range(len(sizes)):
+        ek, ep, P, L = sim.energy(1.0 / 64, c)
+        np.testing.assert_allclose(allc[c], [ek, ep, *P, *L], rtol=1e-13, atol=1e-16)
+    sim.close()
