@@ -273,6 +273,71 @@ double orc_dt_quantize_initial(double dt0, double dt_min, double dt_max)
 }
 
 /* ------------------------------------------------------------------------- */
+/* 4th-order Hermite scheme (Makino & Aarseth 1992): the lower-order member   */
+/* of the family the paper's code inherits from HiGPUs; uses a and jerk only  */
+/* ------------------------------------------------------------------------- */
+
+/* Predictor through jerk: xp = x + v d + a d^2/2 + j d^3/6, vp = v + a d + j d^2/2. */
+void orc_predict4(int64_t n, const double *x, const double *v, const double *a,
+                  const double *j, const double *t, double t_next, double *xp, double *vp)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double dt = t_next - t[i];
+        double d2 = dt * dt / 2.0, d3 = dt * dt * dt / 6.0;
+        for (int d = 0; d < 3; d++) {
+            const int64_t o = 3 * i + d;
+            xp[o] = x[o] + v[o] * dt + a[o] * d2 + j[o] * d3;
+            vp[o] = v[o] + a[o] * dt + j[o] * d2;
+        }
+    }
+}
+
+/*
+ * 4th-order Hermite corrector, h = t1 - t0:
+ *   v1 = v0 + h/2 (a0 + a1) + h^2/12 (j0 - j1)
+ *   x1 = x0 + h/2 (v0 + v1) + h^2/12 (a0 - a1)
+ */
+void orc_correct4(double h, const double x0[3], const double v0[3], const double a0[3],
+                  const double j0[3], const double a1[3], const double j1[3],
+                  double x1[3], double v1[3])
+{
+    for (int d = 0; d < 3; d++) {
+        v1[d] = v0[d] + h / 2.0 * (a0[d] + a1[d]) + h * h / 12.0 * (j0[d] - j1[d]);
+        x1[d] = x0[d] + h / 2.0 * (v0[d] + v1[d]) + h * h / 12.0 * (a0[d] - a1[d]);
+    }
+}
+
+/*
+ * The cubic through (a, j) at t0 and t1: its 2nd and 3rd derivatives at t1.
+ * With p(u) = a0 + j0 u + c2 u^2 + c3 u^3, u = t - t0, p(h) = a1, p'(h) = j1:
+ *   c2 = (3 (a1 - a0) - h (2 j0 + j1)) / h^2,  c3 = (2 (a0 - a1) + h (j0 + j1)) / h^3,
+ *   a''(t1) = 2 c2 + 6 c3 h,  a'''(t1) = 6 c3.
+ */
+void orc_interp4(double h, const double a0[3], const double j0[3], const double a1[3],
+                 const double j1[3], double s1[3], double c1[3])
+{
+    for (int d = 0; d < 3; d++) {
+        double c2 = (3.0 * (a1[d] - a0[d]) - h * (2.0 * j0[d] + j1[d])) / (h * h);
+        double c3 = (2.0 * (a0[d] - a1[d]) + h * (j0[d] + j1[d])) / (h * h * h);
+        s1[d] = 2.0 * c2 + 6.0 * c3 * h;
+        c1[d] = 6.0 * c3;
+    }
+}
+
+/* Aarseth's criterion: dt = sqrt(eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)). */
+double orc_dt_aarseth(const double a[3], const double j[3], const double s[3],
+                      const double c[3], double eta)
+{
+    double an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    double jn = sqrt(j[0] * j[0] + j[1] * j[1] + j[2] * j[2]);
+    double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    double cn = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    double den = jn * cn + sn * sn;
+    if (!(den > 0.0)) return INFINITY;
+    return sqrt(eta * (an * sn + jn * jn) / den);
+}
+
+/* ------------------------------------------------------------------------- */
 /* The integrator: start-up, block step, run, diagnostics                     */
 /* ------------------------------------------------------------------------- */
 
@@ -287,6 +352,7 @@ typedef struct {
     int64_t *act;                      /* [n] */
     double *fa, *fj, *fs, *fp;         /* [n][3], [n] evaluation output */
     int64_t n_underflow;
+    int order;                         /* 6 (default) or 4 */
 } orc_sim;
 
 size_t orc_sim_sizeof(void) { return sizeof(orc_sim); }
@@ -343,7 +409,9 @@ void orc_init(orc_sim *S)
             S->a[3 * i + d] = S->j[3 * i + d] = S->s[3 * i + d] = S->c[3 * i + d] = 0.0;
         }
     }
-    for (int pass = 0; pass < 2; pass++) {
+    /* the 4th-order scheme needs no snap: one pass (a = 0 in the predictor) */
+    const int passes = S->order == 4 ? 1 : 2;
+    for (int pass = 0; pass < passes; pass++) {
         orc_predict(n, S->x, S->v, S->a, S->j, S->s, S->c, S->t, 0.0, S->xp, S->vp, S->ap);
         orc_force(n, S->m, S->xp, S->vp, S->ap, S->eps2, n, S->act, S->fa, S->fj, S->fs, S->fp);
         for (int64_t i = 0; i < n; i++) {
@@ -386,10 +454,52 @@ int64_t orc_select(const orc_sim *S, double *t_next, int64_t *act)
  * set on the predicted state, correct, interpolate the higher derivatives,
  * set the new power-of-two step.  Returns the number of active particles.
  */
+/* 4th-order block step: predictor through jerk, a and jerk evaluated (the
+ * relative accelerations are set to zero, snap is not used), 4th-order
+ * corrector, cubic-interpolated 2nd/3rd derivatives (kept in s and c),
+ * Aarseth's criterion, the same power-of-two quantisation. */
+static int64_t orc_block_step4(orc_sim *S, double tn, int64_t na)
+{
+    orc_predict4(S->n, S->x, S->v, S->a, S->j, S->t, tn, S->xp, S->vp);
+    for (int64_t q = 0; q < 3 * S->n; q++) S->ap[q] = 0.0;
+    orc_force(S->n, S->m, S->xp, S->vp, S->ap, S->eps2, na, S->act, S->fa, S->fj, S->fs, S->fp);
+    for (int64_t k = 0; k < na; k++) {
+        const int64_t i = S->act[k];
+        double *x = &S->x[3 * i], *v = &S->v[3 * i], *a = &S->a[3 * i];
+        double *jj = &S->j[3 * i], *s = &S->s[3 * i], *c = &S->c[3 * i];
+        const double *a1 = &S->fa[3 * k], *j1 = &S->fj[3 * k];
+        double h = tn - S->t[i];
+        double x1[3], v1[3], s1[3], c1[3];
+        orc_correct4(h, x, v, a, jj, a1, j1, x1, v1);
+        orc_interp4(h, a, jj, a1, j1, s1, c1);
+        double dtc = orc_dt_aarseth(a1, j1, s1, c1, S->eta);
+        int uf = 0;
+        double dtn = orc_dt_quantize(dtc, S->dt[i], tn, S->dt_min, S->dt_max, &uf);
+        if (uf) S->n_underflow++;
+        for (int d = 0; d < 3; d++) {
+            x[d] = x1[d];
+            v[d] = v1[d];
+            a[d] = a1[d];
+            jj[d] = j1[d];
+            s[d] = s1[d];
+            c[d] = c1[d];
+        }
+        S->pot[i] = S->fp[k];
+        S->t[i] = tn;
+        S->dt[i] = dtn;
+    }
+    return na;
+}
+
 int64_t orc_block_step(orc_sim *S, double *t_next_out)
 {
     double tn;
     int64_t na = orc_select(S, &tn, S->act);
+    if (S->order == 4) {
+        orc_block_step4(S, tn, na);
+        if (t_next_out) *t_next_out = tn;
+        return na;
+    }
     orc_predict(S->n, S->x, S->v, S->a, S->j, S->s, S->c, S->t, tn, S->xp, S->vp, S->ap);
     orc_force(S->n, S->m, S->xp, S->vp, S->ap, S->eps2, na, S->act, S->fa, S->fj, S->fs, S->fp);
     for (int64_t k = 0; k < na; k++) {
@@ -455,7 +565,10 @@ void orc_energy(orc_sim *S, double t, double *ekin, double *epot, double P[3],
                 double L[3])
 {
     const int64_t n = S->n;
-    orc_predict(n, S->x, S->v, S->a, S->j, S->s, S->c, S->t, t, S->xp, S->vp, S->ap);
+    if (S->order == 4)
+        orc_predict4(n, S->x, S->v, S->a, S->j, S->t, t, S->xp, S->vp);
+    else
+        orc_predict(n, S->x, S->v, S->a, S->j, S->s, S->c, S->t, t, S->xp, S->vp, S->ap);
     for (int64_t i = 0; i < n; i++) S->act[i] = i;
     orc_force(n, S->m, S->xp, S->vp, S->ap, S->eps2, n, S->act, S->fa, S->fj, S->fs, S->fp);
     double ek = 0, ep = 0, p[3] = {0, 0, 0}, l[3] = {0, 0, 0};
@@ -478,6 +591,14 @@ void orc_energy(orc_sim *S, double t, double *ekin, double *epot, double P[3],
 }
 
 int64_t orc_underflows(const orc_sim *S) { return S->n_underflow; }
+
+/* Integration order of the simulation: 6 (default) or 4.  Call before orc_init. */
+int orc_set_order(orc_sim *S, int order)
+{
+    if (order != 4 && order != 6) return 1;
+    S->order = order;
+    return 0;
+}
 
 int orc_num_threads(void)
 {

@@ -77,6 +77,13 @@ def lib():
             L.orc_underflows.argtypes = [C.c_void_p]
             L.orc_underflows.restype = C.c_int64
             L.orc_num_threads.restype = C.c_int
+            L.orc_predict4.argtypes = [C.c_int64] + [_D] * 5 + [C.c_double, _D, _D]
+            L.orc_correct4.argtypes = [C.c_double] + [_D] * 8
+            L.orc_interp4.argtypes = [C.c_double] + [_D] * 6
+            L.orc_dt_aarseth.argtypes = [_D] * 4 + [C.c_double]
+            L.orc_dt_aarseth.restype = C.c_double
+            L.orc_set_order.argtypes = [C.c_void_p, C.c_int]
+            L.orc_set_order.restype = C.c_int
             _lib = L
     return _lib
 
@@ -148,6 +155,35 @@ def dt_initial(a, j, s, eta_init):
     return float(lib().orc_dt_initial(*[_p(q) for q in args], float(eta_init)))
 
 
+def predict4(x, v, a, j, t, t_next):
+    """4th-order predictor (through jerk): (xp, vp)."""
+    n = np.asarray(t).shape[0]
+    x, v, a, j = (_f64(q, (n, 3)) for q in (x, v, a, j))
+    t = _f64(t)
+    xp = np.zeros((n, 3)); vp = np.zeros((n, 3))
+    lib().orc_predict4(n, _p(x), _p(v), _p(a), _p(j), _p(t), float(t_next), _p(xp), _p(vp))
+    return xp, vp
+
+
+def correct4(h, x0, v0, a0, j0, a1, j1):
+    args = [_f64(q, (3,)) for q in (x0, v0, a0, j0, a1, j1)]
+    x1 = np.zeros(3); v1 = np.zeros(3)
+    lib().orc_correct4(float(h), *[_p(q) for q in args], _p(x1), _p(v1))
+    return x1, v1
+
+
+def interp4(h, a0, j0, a1, j1):
+    args = [_f64(q, (3,)) for q in (a0, j0, a1, j1)]
+    s1 = np.zeros(3); c1 = np.zeros(3)
+    lib().orc_interp4(float(h), *[_p(q) for q in args], _p(s1), _p(c1))
+    return s1, c1
+
+
+def dt_aarseth(a, j, s, c, eta):
+    args = [_f64(q, (3,)) for q in (a, j, s, c)]
+    return float(lib().orc_dt_aarseth(*[_p(q) for q in args], float(eta)))
+
+
 def dt_quantize(dt_crit, dt_old, t1, dt_min, dt_max):
     uf = C.c_int(0)
     r = lib().orc_dt_quantize(float(dt_crit), float(dt_old), float(t1), float(dt_min),
@@ -160,14 +196,14 @@ def dt_quantize_initial(dt0, dt_min, dt_max):
 
 
 class Sim:
-    """FP64 block-time-step Hermite-6 integrator (oracle).
+    """FP64 block-time-step Hermite integrator (oracle), 6th order or 4th order.
 
     State arrays are numpy attributes in the oracle layout:
     ``m (n,)``, ``x v a j s c (n,3)``, ``t dt pot (n,)``.
     """
 
     def __init__(self, m, x, v, eps, eta=0.4, eta_init=0.01,
-                 dt_min=2.0 ** -20, dt_max=2.0 ** -3):
+                 dt_min=2.0 ** -20, dt_max=2.0 ** -3, order=6):
         L = lib()
         self.n = n = int(np.asarray(m).shape[0])
         self.m = _f64(m).copy()
@@ -185,6 +221,9 @@ class Sim:
                         _p(self.pot))
         if rc != 0:
             raise MemoryError("oracle: allocation failed")
+        if L.orc_set_order(self._buf, int(order)) != 0:
+            raise ValueError("oracle: order must be 4 or 6")
+        self.order = int(order)
         self.block_steps = 0
         self.interactions = 0.0
 
@@ -196,7 +235,7 @@ class Sim:
 
     def init(self):
         lib().orc_init(self._buf)
-        self.interactions += 2.0 * self.n * (self.n - 1)
+        self.interactions += (1.0 if self.order == 4 else 2.0) * self.n * (self.n - 1)
         return self
 
     def select(self):
