@@ -465,6 +465,57 @@ def config3_case(args):
     print(json.dumps(out))
 
 
+def _lagrangian_radii(m, x, fractions=(0.1, 0.5, 0.9)):
+    com = (m[:, None] * x).sum(0) / m.sum()
+    r = np.linalg.norm(x - com, axis=1)
+    order = np.argsort(r)
+    cm = np.cumsum(m[order]) / m.sum()
+    return [float(r[order][np.searchsorted(cm, f)]) for f in fractions]
+
+
+def config2_check(args):
+    """The benchmark's integration run to t = 0.25 on the GPU (FP64 and EX)
+    and by the CPU oracle: block steps, interactions, energy error, momentum
+    and Lagrangian radii at the end (block-step runs diverge per particle, so
+    the comparison is statistical)."""
+    import torch
+    from oracle import nb_oracle
+    from paper_1812_00367_gb300 import build as nbbuild
+    from paper_1812_00367_gb300 import ic, nb
+    nbbuild.build()
+    nb.load()
+    nb_oracle.build()
+    dev = torch.device("cuda", 0)
+    m, x, v = ic.plummer(N, seed=SEED)
+    out = {"case": "config2_check", "n": N, "t_end": T_END}
+    for prec in ("fp64", "ex"):
+        sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX, precision=prec)
+        ek0, ep0, P0, L0 = sim.energy(0.0)
+        steps, inter, sec = _timed_run(sim, torch, dev, T_END)
+        ek1, ep1, P1, L1 = sim.energy(T_END)
+        st = sim.state_numpy()
+        out[prec] = {"block_steps": steps, "interactions": inter, "seconds": sec,
+                     "interactions_per_s": inter / sec,
+                     "rel_energy_error": abs((ek1 + ep1) - (ek0 + ep0)) / abs(ek0 + ep0),
+                     "dP": float(np.linalg.norm(P1 - P0)), "dL": float(np.linalg.norm(L1 - L0)),
+                     "lagrangian_radii_10_50_90": _lagrangian_radii(m, st["x"]),
+                     "dt_underflows": sim.counters()["dt_underflows"]}
+        sim.close()
+    t0 = time.perf_counter()
+    ref = nb_oracle.Sim(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX).init()
+    e0 = ref.energy(0.0)
+    ref.run(T_END)
+    e1 = ref.energy(T_END)
+    sec = time.perf_counter() - t0
+    out["oracle"] = {"block_steps": ref.block_steps, "interactions": ref.interactions,
+                     "seconds_incl_startup": sec, "threads": nb_oracle.num_threads(),
+                     "rel_energy_error": abs((e1[0] + e1[1]) - (e0[0] + e0[1])) / abs(e0[0] + e0[1]),
+                     "dP": float(np.linalg.norm(e1[2] - e0[2])), "dL": float(np.linalg.norm(e1[3] - e0[3])),
+                     "lagrangian_radii_10_50_90": _lagrangian_radii(m, ref.x),
+                     "dt_underflows": ref.underflows}
+    print(json.dumps(out))
+
+
 def merger_case(args):
     """Two Hernquist spheres of 2^21 particles each on a parabolic orbit,
     eps = 1e-3: evaluation throughput of an active subset against all
@@ -583,7 +634,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default plan table")
     ap.add_argument("--slice", type=float, default=SLICE,
                     help="N-body time per step (a power of two dividing 0.25); shorter for profiling")
-    ap.add_argument("--case", choices=["run", "eval", "batched", "config3", "merger"], default="run")
+    ap.add_argument("--case", choices=["run", "eval", "batched", "config3", "merger", "config2-check"],
+                    default="run")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--batched-target", type=int, default=0,
                     help="split target per cluster for --case batched (0: library default)")
@@ -601,7 +653,7 @@ def main():
     args = ap.parse_args()
     if args.case != "run":
         {"eval": eval_case, "batched": batched_case, "config3": config3_case,
-         "merger": merger_case}[args.case](args)
+         "merger": merger_case, "config2-check": config2_check}[args.case](args)
         return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()

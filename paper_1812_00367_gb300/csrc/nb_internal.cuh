@@ -138,7 +138,6 @@ struct EvalLaunch {
     int32_t identity;   // active list is 0..A-1 of the cluster (init, energy)
     const int32_t *active;  // direct mode list (global indices)
     double *out;        // direct mode output [10][n_active]
-    double t_next;      // unused in plan mode (per-cluster tnext)
 };
 
 enum EvalMode { kModeOut = 0, kModeStep = 1, kModeInit1 = 2, kModeInit2 = 3, kModePot = 4 };
@@ -245,7 +244,6 @@ struct ff {
     float hi, lo;
 };
 
-__device__ __forceinline__ ff ff_make(float h, float l) { return ff{h, l}; }
 
 // exact: s + e = a + b (Knuth TwoSum)
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -394,7 +392,6 @@ cudaError_t launch_correct(const Dev &d, int64_t lo, int64_t hi, const int32_t *
                            int32_t n_active, double t_next, const double *ajs, cudaStream_t st);
 cudaError_t launch_init_clear(const Dev &d, cudaStream_t st);
 cudaError_t launch_energy(const Dev &d, int64_t begin, int64_t end, int blocks, cudaStream_t st);
-cudaError_t launch_fill_identity(const Dev &d, cudaStream_t st);
 int eval_occupancy(int precision, int mode);  // CTAs per SM
 
 }  // namespace nb
