@@ -44,6 +44,30 @@ UNIT = "interactions/s"
 WORKLOAD = (f"Plummer N={N}, equal masses, Henon units, eps={EPS:g}, block steps "
             f"dt in [2^-20, 2^-3], eta={ETA}, integrated to t={T_END} in slices of 1/64")
 
+# DRAM traffic of the FP64 step-evaluation kernel, bytes per launch: the mean
+# of dram__bytes_read.sum + dram__bytes_write.sum over every k_eval<FP64, step>
+# launch of one ncu capture of this workload (summary and command in
+# profiles/).  It holds for the kernel sources it was taken on (SHA-256 of
+# EVAL_SOURCES below); after any change to them it is reported as null.
+EVAL_TRAFFIC = {"bytes_per_launch": None, "launches": None, "sources_sha256": None}
+EVAL_SOURCES = ("nb_eval.cuh", "nb_eval_fp64.cu", "nb_step.cuh", "nb_internal.cuh")
+
+
+def eval_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in EVAL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1812_00367_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def eval_traffic():
+    """Measured bytes per launch if the kernel is unchanged since, else None."""
+    if EVAL_TRAFFIC["bytes_per_launch"] is None:
+        return None
+    return EVAL_TRAFFIC["bytes_per_launch"] if eval_sources_sha256() == EVAL_TRAFFIC["sources_sha256"] else None
+
 
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -273,7 +297,8 @@ def gpu_arm(args, ws, rank, local):
                      "peak": peak64 / 1e12, "unit": "TFLOP/s",
                      "peak_source": "FP64 FMA probe (nb_probe_fma_peak) in this run",
                      "frac": None if achieved is None else achieved / peak64,
-                     "traffic": None,
+                     "traffic": eval_traffic(),
+                     "traffic_unit": "DRAM bytes per launch (ncu), null if the kernel changed",
                      "avg_launch_ms": eval_avg_ms, "launches": r64["eval_launches"],
                      "share_of_step_time": r64["eval_ms"] / r64["ms"] if r64["ms"] else None,
                      "flops_per_interaction": FLOPS_PER_INTERACTION},
@@ -305,13 +330,13 @@ def gpu_arm(args, ws, rank, local):
     return out
 
 
-def eval_rate(nb, torch, dev, m, x, v, precision, A, reps):
+def eval_rate(nb, torch, dev, m, x, v, precision, A, reps, order=6):
     """Evaluation-kernel throughput: A active particles against all N of the
     start-up state (nb_predict then nb_evaluate), CUDA events on the stream."""
     n = len(m)
     # no start-up evaluations: the launches of this case are the timed ones
     sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX,
-                        precision=precision, keep_state=True)
+                        precision=precision, keep_state=True, order=order)
     sim.predict(0.0, out=False)
     act = torch.arange(A, dtype=torch.int32, device=dev)
     out = torch.empty((10, A), dtype=torch.float64, device=dev)
@@ -555,6 +580,46 @@ def merger_case(args):
     print(json.dumps(out))
 
 
+ETA4 = 0.02
+
+
+def order4_case(args):
+    """The 4th-order Hermite variant on the headline workload (Plummer
+    N=65536, eps=1e-4, block steps, eta=0.02): block-step throughput from
+    t_warm over t_run, its evaluation share (CUDA events inside the graphs),
+    the energy drift over the timed run, and the all-active evaluation
+    kernel rate, in FP64, EX and FP32; the 6th-order FP64 run beside it."""
+    import torch
+    from paper_1812_00367_gb300 import build as nbbuild
+    from paper_1812_00367_gb300 import ic, nb
+    nbbuild.build()
+    nb.load()
+    dev = torch.device("cuda", 0)
+    m, x, v = ic.plummer(N, seed=SEED)
+    out = {"case": "order4", "n": N, "eps": EPS, "eta4": ETA4, "eta6": ETA,
+           "t_warm": args.t_warm, "t_run": args.t_run}
+    runs = [("fp64", 4), ("ex", 4), ("fp32", 4), ("fp64", 6)]
+    for prec, order in runs:
+        sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA4 if order == 4 else ETA, dt_min=DT_MIN,
+                            dt_max=DT_MAX, precision=prec, order=order, time_eval=True)
+        sim.run(args.t_warm)
+        e0 = sum(sim.energy(args.t_warm)[:2])
+        c0 = sim.counters()
+        steps, inter, sec = _timed_run(sim, torch, dev, args.t_warm + args.t_run)
+        c1 = sim.counters()
+        e1 = sum(sim.energy(args.t_warm + args.t_run)[:2])
+        ev_ms = c1["eval_ms"] - c0["eval_ms"]
+        sim.close()
+        r = eval_rate(nb, torch, dev, m, x, v, prec, N, 2, order=order)
+        out[f"{prec}/order{order}"] = {
+            "block_steps": steps, "interactions": inter, "seconds": sec,
+            "interactions_per_s": inter / sec,
+            "eval_interactions_per_s": inter / (ev_ms * 1e-3) if ev_ms > 0 else None,
+            "energy_drift": abs(e1 - e0) / abs(e0),
+            "all_active_eval_per_s": r["interactions_per_s"]}
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------ CPU oracle
 def _oracle_setup():
     from oracle import nb_oracle
@@ -634,7 +699,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default plan table")
     ap.add_argument("--slice", type=float, default=SLICE,
                     help="N-body time per step (a power of two dividing 0.25); shorter for profiling")
-    ap.add_argument("--case", choices=["run", "eval", "batched", "config3", "merger", "config2-check"],
+    ap.add_argument("--case", choices=["run", "eval", "batched", "config3", "merger", "config2-check",
+                                       "order4"],
                     default="run")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--batched-target", type=int, default=0,
@@ -653,7 +719,8 @@ def main():
     args = ap.parse_args()
     if args.case != "run":
         {"eval": eval_case, "batched": batched_case, "config3": config3_case,
-         "merger": merger_case, "config2-check": config2_check}[args.case](args)
+         "merger": merger_case, "config2-check": config2_check,
+         "order4": order4_case}[args.case](args)
         return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()

@@ -75,6 +75,16 @@ typedef struct {
                         dt_min == dt_max gives shared steps */
     int32_t precision; /* nb_precision */
     uint32_t flags;    /* NB_INIT_* */
+    int32_t order;     /* integration order: 6 (0 means 6) = the NM08 6th-order
+                          scheme above; 4 = the 4th-order Hermite scheme of
+                          Makino & Aarseth 1992 (predictor through jerk,
+                          a and jerk evaluated, s = 0 in nb_evaluate's
+                          output, Aarseth's criterion
+                          dt = sqrt(eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2))
+                          on the cubic-interpolated a2, a3 kept in s and c;
+                          one start-up pass, dt0 = eta_init |a|/|j|);
+                          any other value: NB_EINVAL */
+    int32_t reserved;  /* must be 0 */
 } nb_params;
 
 /* Particle state: caller-owned DEVICE buffers that must stay alive for the
@@ -103,7 +113,8 @@ typedef struct {
  * (Hermite-6 needs snap, which needs the other particles' accelerations:
  * pass 1 evaluates a and jerk with a = 0, pass 2 evaluates snap with that a;
  * crackle starts at 0; t = 0; dt from the start-up rule, a power of two in
- * [dt_min, dt_max]).  With NB_INIT_KEEP_STATE the state is taken as is.
+ * [dt_min, dt_max]).  With order 4 only pass 1 runs (s = c = 0).  With
+ * NB_INIT_KEEP_STATE the state is taken as is.
  *
  *   out             : receives the new context (NULL on failure)
  *   p               : parameters (copied)
@@ -117,7 +128,8 @@ typedef struct {
  *                     cluster
  *   stream          : cudaStream_t to enqueue on (NULL = legacy default)
  * Errors: NB_EINVAL (n < 1, bad offsets, eps < 0, eta <= 0, dt_min/dt_max
- * not powers of two or dt_min > dt_max, unknown precision), NB_ENOMEM,
+ * not powers of two or dt_min > dt_max, unknown precision or order,
+ * reserved != 0), NB_ENOMEM,
  * NB_ECUDA.  Allocates the library's scratch (predicted j-arrays, active
  * lists, partial sums, graphs); nb_free releases it.
  */
@@ -132,7 +144,9 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
  *   a_p = a + j d + s d^2/2 + c d^3/6
  * into the context's packed j-array (in the context's precision), which the
  * next nb_evaluate reads.  out: optional DEVICE [10][n] double receiving
- * x_p[3], v_p[3], a_p[3], m (NULL to skip).  Errors: NB_EINVAL, NB_ECUDA.
+ * x_p[3], v_p[3], a_p[3], m (NULL to skip).  With order 4 the series stops
+ * at the jerk term (s and c are then the criterion's interpolated
+ * derivatives, not predictor terms).  Errors: NB_EINVAL, NB_ECUDA.
  */
 nb_status nb_predict(nb_ctx *ctx, double t_next, double *out);
 
@@ -146,6 +160,7 @@ nb_status nb_predict(nb_ctx *ctx, double t_next, double *out);
  *   jerk += m_j v / s2^{3/2} - 3 alpha A0            (A1)
  *   snap += m_j a / s2^{3/2} - 6 alpha A1 - 3 beta A0 (A2)
  *   pot  -= m_j / s2^{1/2}
+ * With order 4 only A0, A1 and pot are summed (a is not read; snap = 0).
  * j == i is excluded by index.  The j range may be split across thread
  * blocks; partial sums are combined in a fixed order (deterministic).
  *   active  : DEVICE int32 [n_active], global particle indices inside the
@@ -169,6 +184,12 @@ nb_status nb_evaluate(nb_ctx *ctx, int32_t cluster, const int32_t *active, int32
  * 2 dt; clamp to [dt_min, dt_max]), and t_i = t_next, c = a^(3)(t_next).
  *   active : DEVICE int32 [n_active] (no duplicates), in cluster `cluster`
  *   ajs    : DEVICE double [10][n_active] as written by nb_evaluate
+ * With order 4: the Makino & Aarseth corrector
+ *   v1 = v0 + h/2 (a0 + a1) + h^2/12 (j0 - j1)
+ *   x1 = x0 + h/2 (v0 + v1) + h^2/12 (a0 - a1),
+ * the 2nd and 3rd derivatives at t_next of the cubic matching (a, j) at
+ * both ends (stored in s and c), and Aarseth's criterion (see nb_params),
+ * with the same quantisation.
  * Errors: NB_EINVAL, NB_ECUDA.  Non-finite results set the device error word.
  */
 nb_status nb_correct_and_timestep(nb_ctx *ctx, int32_t cluster, const int32_t *active,

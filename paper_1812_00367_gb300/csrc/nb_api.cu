@@ -160,7 +160,8 @@ cudaError_t enqueue_step(nb_ctx *ctx, cudaStream_t st, int slot) {
     EvalLaunch L{};
     if (slot >= 0 && (e = cudaEventRecordWithFlags(ctx->ev[2 * slot], st, cudaEventRecordExternal)) != cudaSuccess)
         return e;
-    if ((e = launch_eval(ctx->d, kModeStep, L, ctx->grid_eval, st)) != cudaSuccess) return e;
+    const int mode = ctx->d.order == 4 ? kModeStep4 : kModeStep;
+    if ((e = launch_eval(ctx->d, mode, L, ctx->grid_eval, st)) != cudaSuccess) return e;
     if (slot >= 0 && (e = cudaEventRecordWithFlags(ctx->ev[2 * slot + 1], st, cudaEventRecordExternal)) != cudaSuccess)
         return e;
     return cudaSuccess;
@@ -238,20 +239,22 @@ nb_status eval_direct(nb_ctx *ctx, int cluster, const int32_t *active, int32_t n
     L.out = out;
     const int64_t items = (int64_t)tiles * split;
     const int grid = (int)std::min<int64_t>(items, ctx->grid_eval);
-    NB_CU(ctx, launch_eval(ctx->d, kModeOut, L, grid, ctx->stream));
+    NB_CU(ctx, launch_eval(ctx->d, ctx->d.order == 4 ? kModeOut4 : kModeOut, L, grid, ctx->stream));
     return NB_OK;
 }
 
-// Start-up: the two evaluation passes (a, jerk with a = 0; then snap), dt0.
+// Start-up: the two evaluation passes (a, jerk with a = 0; then snap), dt0;
+// the 4th-order scheme takes the first pass only (a, jerk; dt0 from |a|/|j|).
 nb_status startup(nb_ctx *ctx) {
     NB_CU(ctx, launch_init_clear(ctx->d, ctx->stream));
-    for (int pass = 0; pass < 2; ++pass) {
+    const bool order4 = ctx->d.order == 4;
+    for (int pass = 0; pass < (order4 ? 1 : 2); ++pass) {
         NB_CU(ctx, launch_predict(ctx->d, 0, 1, 0.0, ctx->stream));
         NB_CU(ctx, launch_plan_ex(ctx->d, 1, 0, ctx->stream));
         EvalLaunch L{};
         L.identity = 1;
-        NB_CU(ctx, launch_eval(ctx->d, pass == 0 ? kModeInit1 : kModeInit2, L, ctx->grid_eval,
-                               ctx->stream));
+        const int mode = order4 ? kModeInit4 : (pass == 0 ? kModeInit1 : kModeInit2);
+        NB_CU(ctx, launch_eval(ctx->d, mode, L, ctx->grid_eval, ctx->stream));
     }
     return NB_OK;
 }
@@ -309,6 +312,9 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
         return fail(nullptr, NB_EINVAL, "nb_init: dt_min/dt_max must be powers of two, min <= max");
     if (p->precision < NB_FP64 || p->precision > NB_FP32)
         return fail(nullptr, NB_EINVAL, "nb_init: unknown precision");
+    if (p->order != 0 && p->order != 4 && p->order != 6)
+        return fail(nullptr, NB_EINVAL, "nb_init: order must be 4 or 6 (0 = 6)");
+    if (p->reserved != 0) return fail(nullptr, NB_EINVAL, "nb_init: reserved must be 0");
     if (!st->m || !st->x || !st->v || !st->a || !st->j || !st->s || !st->c || !st->t || !st->dt || !st->pot)
         return fail(nullptr, NB_EINVAL, "nb_init: NULL state buffer");
     std::vector<int64_t> offs(n_clusters + 1);
@@ -365,6 +371,7 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     d.n_clusters = n_clusters;
     d.n_chunks = n_chunks;
     d.precision = p->precision;
+    d.order = p->order == 4 ? 4 : 6;
     d.m = st->m; d.x = st->x; d.v = st->v; d.a = st->a; d.j = st->j; d.s = st->s; d.c = st->c;
     d.t = st->t; d.dt = st->dt; d.pot = st->pot;
     d.eps2 = p->eps * p->eps;
@@ -375,7 +382,7 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     d.neg_one = -1.0;
     d.neg_zero = -0.0;
 
-    const int occ = std::max(1, eval_occupancy(p->precision, kModeStep));
+    const int occ = std::max(1, eval_occupancy(p->precision, d.order == 4 ? kModeStep4 : kModeStep));
     ctx->grid_eval = occ * ctx->sm_count;
     ctx->grid_pot = std::max(1, eval_occupancy(NB_FP64, kModePot)) * ctx->sm_count;
     d.grid_eval = ctx->grid_eval;

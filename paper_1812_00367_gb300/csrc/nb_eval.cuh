@@ -13,7 +13,8 @@
 // (that keeps the FP32 path within its bound on strongly cancelling sums).
 // Every per-pair operation is a multiply, an add or a fused multiply-add:
 // 53 FP64 instructions per pair on the FP64 path (one exact doubling is done
-// on the integer pipe).
+// on the integer pipe).  The 4th-order scheme (Makino & Aarseth 1992) keeps
+// A0, A1 and the potential only (interact4: 32 FP64 instructions per pair).
 //
 // Work decomposition: a work item is (cluster, i-tile, j-range).  An i-tile
 // holds kTPB / gl active particles; gl lanes of a warp share one i and take
@@ -105,6 +106,27 @@ struct Prec<NB_FP64> {
         c.a[0] = fma(q, rx, c.a[0]); c.a[1] = fma(q, ry, c.a[1]); c.a[2] = fma(q, rz, c.a[2]);
         c.j[0] = fma(q, w1x, c.j[0]); c.j[1] = fma(q, w1y, c.j[1]); c.j[2] = fma(q, w1z, c.j[2]);
         c.s[0] = fma(q, w2x, c.s[0]); c.s[1] = fma(q, w2y, c.s[1]); c.s[2] = fma(q, w2z, c.s[2]);
+    }
+    // 4th-order pair term (Makino & Aarseth 1992): A0 = q r, A1 = q (v - 3 alpha r);
+    // 32 FP64 instructions
+    static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self,
+                                                     double eps2, float, Acc &c) {
+        const double2 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
+        const double rx = sub(i, q0.x, i.x[0]), ry = sub(i, q0.y, i.x[1]), rz = sub(i, q1.x, i.x[2]);
+        const double vx = sub(i, q2.x, i.v[0]), vy = sub(i, q2.y, i.v[1]), vz = sub(i, q3.x, i.v[2]);
+        double r2 = fma(rx, rx, fma(ry, ry, fma(rz, rz, eps2)));
+        double m = q1.y;
+        r2 = self ? 1.0 : r2;
+        m = self ? 0.0 : m;
+        const double y = NB_FP64_ALL_FMA ? rsqrt_f64_fma(r2, i.nz) : rsqrt_f64(r2);
+        const double y2 = mul(i, y, y);
+        c.p = fma(m, y, c.p);
+        const double q = mul(i, mul(i, m, y2), y);
+        const double rv = fma(rx, vx, fma(ry, vy, mul(i, rz, vz)));
+        const double al3 = mul(i, 3.0, mul(i, rv, y2));
+        const double w1x = fma(-al3, rx, vx), w1y = fma(-al3, ry, vy), w1z = fma(-al3, rz, vz);
+        c.a[0] = fma(q, rx, c.a[0]); c.a[1] = fma(q, ry, c.a[1]); c.a[2] = fma(q, rz, c.a[2]);
+        c.j[0] = fma(q, w1x, c.j[0]); c.j[1] = fma(q, w1y, c.j[1]); c.j[2] = fma(q, w1z, c.j[2]);
     }
     // pot-only pair term (energy diagnostics)
     static __device__ __forceinline__ void interact_pot(const I &i, const J &jj, bool self,
@@ -206,6 +228,35 @@ struct Prec<NB_EX> {
             ff_fma_acc(c.s[k], q, w2);
         }
     }
+    static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self, double,
+                                                     float, Acc &c, ff eps2) {
+        const float4 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
+        ff r[3], v[3];
+        r[0] = ff_sub(ff{q0.x, q1.x}, i.x[0]);
+        r[1] = ff_sub(ff{q0.y, q1.y}, i.x[1]);
+        r[2] = ff_sub(ff{q0.z, q1.z}, i.x[2]);
+        v[0] = ff_sub(ff{q2.x, q3.x}, i.v[0]);
+        v[1] = ff_sub(ff{q2.y, q3.y}, i.v[1]);
+        v[2] = ff_sub(ff{q2.z, q3.z}, i.v[2]);
+        ff r2 = ff_add(ff_dot3(r, r), eps2);
+        ff m = ff{q0.w, q1.w};
+        if (self) {
+            r2 = ff{1.f, 0.f};
+            m = ff{0.f, 0.f};
+        }
+        const ff y = rsqrt_ff(r2);
+        const ff y2 = ff_sqr(y);
+        const ff my = ff_mul(m, y);
+        const ff q = ff_mul(my, y2);
+        c.p = ff_add(c.p, my);
+        const ff al3 = ff_mul_f(ff_mul(ff_dot3(r, v), y2), 3.0f);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const ff w1 = ff_fnma(al3, r[k], v[k]);
+            ff_fma_acc(c.a[k], q, r[k]);
+            ff_fma_acc(c.j[k], q, w1);
+        }
+    }
     static __device__ __forceinline__ double to_d(ff a) { return (double)a.hi + (double)a.lo; }
     static __device__ __forceinline__ void finish(const Acc &c, const double *, double o[10]) {
 #pragma unroll
@@ -284,6 +335,32 @@ struct Prec<NB_FP32> {
         c.j[0] = fmaf(q, w1x, c.j[0]); c.j[1] = fmaf(q, w1y, c.j[1]); c.j[2] = fmaf(q, w1z, c.j[2]);
         c.s[0] = fmaf(q, w2x, c.s[0]); c.s[1] = fmaf(q, w2y, c.s[1]); c.s[2] = fmaf(q, w2z, c.s[2]);
     }
+    static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self, double,
+                                                     float eps2, Acc &c) {
+        const float4 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
+        const float rx = (q0.x - i.xh[0]) + (q1.x - i.xl[0]);
+        const float ry = (q0.y - i.xh[1]) + (q1.y - i.xl[1]);
+        const float rz = (q0.z - i.xh[2]) + (q1.z - i.xl[2]);
+        const float vx = (q2.x - i.vh[0]) + (q3.x - i.vl[0]);
+        const float vy = (q2.y - i.vh[1]) + (q3.y - i.vl[1]);
+        const float vz = (q2.z - i.vh[2]) + (q3.z - i.vl[2]);
+        float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
+        float m = q0.w;
+        r2 = self ? 1.f : r2;
+        m = self ? 0.f : m;
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+        const float hr2 = 0.5f * r2;
+        y = y * fmaf(-hr2 * y, y, 1.5f);
+        const float y2 = y * y;
+        const float my = m * y;
+        const float q = my * y2;
+        c.p += my;
+        const float al3 = 3.f * (fmaf(rx, vx, fmaf(ry, vy, rz * vz)) * y2);
+        const float w1x = fmaf(-al3, rx, vx), w1y = fmaf(-al3, ry, vy), w1z = fmaf(-al3, rz, vz);
+        c.a[0] = fmaf(q, rx, c.a[0]); c.a[1] = fmaf(q, ry, c.a[1]); c.a[2] = fmaf(q, rz, c.a[2]);
+        c.j[0] = fmaf(q, w1x, c.j[0]); c.j[1] = fmaf(q, w1y, c.j[1]); c.j[2] = fmaf(q, w1z, c.j[2]);
+    }
     // End of a tile: add the tile sums into the chunk sums.
     static __device__ __forceinline__ void tile_done(Acc &c) {
 #pragma unroll
@@ -338,11 +415,13 @@ __device__ __forceinline__ int find_cluster(const ClusterPlan *plan, int nc, int
 template <int P, int MODE>
 __device__ __forceinline__ void finalize_one(const Dev &d, const EvalLaunch &L, int c, int64_t gi,
                                              int iloc, const double o[10]) {
-    if constexpr (MODE == kModeOut) {
+    if constexpr (MODE == kModeOut || MODE == kModeOut4) {
         for (int q = 0; q < 10; ++q) L.out[(int64_t)q * L.n_active + iloc] = o[q];
     } else if constexpr (MODE == kModeStep) {
         correct_particle(d, gi, d.tnext[c], o);
-    } else if constexpr (MODE == kModeInit1 || MODE == kModeInit2) {
+    } else if constexpr (MODE == kModeStep4) {
+        correct_particle4(d, gi, d.tnext[c], o);
+    } else if constexpr (MODE == kModeInit1 || MODE == kModeInit2 || MODE == kModeInit4) {
         const int64_t n = d.n;
         for (int k = 0; k < 3; ++k) {
             d.a[k * n + gi] = o[k];
@@ -350,7 +429,8 @@ __device__ __forceinline__ void finalize_one(const Dev &d, const EvalLaunch &L, 
             d.s[k * n + gi] = (MODE == kModeInit2) ? o[6 + k] : 0.0;
         }
         d.pot[gi] = o[9];
-        if constexpr (MODE == kModeInit2) d.dt[gi] = dt_start(d, o);
+        // the 4th-order start-up has no snap: dt0 = eta_init |a| / |j|
+        if constexpr (MODE != kModeInit1) d.dt[gi] = dt_start(d, o);
     } else {  // kModePot
         d.pot_tmp[gi] = o[9];
     }
@@ -471,10 +551,18 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
                 if constexpr (MODE == kModePot) {
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact_pot(me, tl[k], jbase + k == ji, eps2, acc);
+                } else if constexpr (P == NB_EX && is_order4_mode(MODE)) {
+#pragma unroll 1
+                    for (int k = jsub; k < kTJ; k += gl)
+                        T::interact4(me, tl[k], jbase + k == ji, eps2, eps2f, acc, eps2ff);
                 } else if constexpr (P == NB_EX) {
 #pragma unroll 1
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact(me, tl[k], jbase + k == ji, eps2, eps2f, acc, eps2ff);
+                } else if constexpr (is_order4_mode(MODE)) {
+#pragma unroll kEvalUnroll
+                    for (int k = jsub; k < kTJ; k += gl)
+                        T::interact4(me, tl[k], jbase + k == ji, eps2, eps2f, acc);
                 } else {
 #pragma unroll kEvalUnroll
                     for (int k = jsub; k < kTJ; k += gl)

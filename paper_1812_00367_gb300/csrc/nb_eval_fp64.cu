@@ -10,6 +10,9 @@ cudaError_t launch_eval_fp64(const Dev &d, int mode, const EvalLaunch &L, int gr
     case kModeStep: return launch_eval_t<NB_FP64, kModeStep>(d, L, grid, st);
     case kModeInit1: return launch_eval_t<NB_FP64, kModeInit1>(d, L, grid, st);
     case kModeInit2: return launch_eval_t<NB_FP64, kModeInit2>(d, L, grid, st);
+    case kModeOut4: return launch_eval_t<NB_FP64, kModeOut4>(d, L, grid, st);
+    case kModeStep4: return launch_eval_t<NB_FP64, kModeStep4>(d, L, grid, st);
+    case kModeInit4: return launch_eval_t<NB_FP64, kModeInit4>(d, L, grid, st);
     case kModePot: return launch_eval_t<NB_FP64, kModePot>(d, L, grid, st);
     default: return cudaErrorInvalidValue;
     }
@@ -17,7 +20,7 @@ cudaError_t launch_eval_fp64(const Dev &d, int mode, const EvalLaunch &L, int gr
 
 int occupancy_fp64(int mode) {
     if (mode == kModePot) return occupancy_t<NB_FP64, kModePot>();
-    (void)mode;
+    if (is_order4_mode(mode)) return occupancy_t<NB_FP64, kModeStep4>();
     return occupancy_t<NB_FP64, kModeStep>();
 }
 

@@ -84,6 +84,7 @@ struct Dev {
     int32_t n_clusters;
     int32_t n_chunks;
     int32_t precision;
+    int32_t order;      // 6: NM08 6th order; 4: Makino & Aarseth 4th order
     int32_t grid_eval;  // persistent evaluation grid (CTAs)
     const int64_t *offsets;      // [nc+1] particle offsets
     const int64_t *jofs;         // [nc+1] padded j-array offsets
@@ -140,7 +141,13 @@ struct EvalLaunch {
     double *out;        // direct mode output [10][n_active]
 };
 
-enum EvalMode { kModeOut = 0, kModeStep = 1, kModeInit1 = 2, kModeInit2 = 3, kModePot = 4 };
+// Out/Step/Init1/Init2: 6th-order pair terms (a, jerk, snap); the *4 modes
+// evaluate the 4th-order terms (a, jerk; snap slots stay 0); Pot: potential.
+enum EvalMode {
+    kModeOut = 0, kModeStep = 1, kModeInit1 = 2, kModeInit2 = 3, kModePot = 4,
+    kModeOut4 = 5, kModeStep4 = 6, kModeInit4 = 7
+};
+constexpr bool is_order4_mode(int mode) { return mode >= kModeOut4; }
 
 // ---------------------------------------------------------- small helpers
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -301,7 +301,8 @@ __global__ void k_correct(const Dev d, const int32_t *active, int32_t n_active, 
     }
     double o[10];
     for (int q = 0; q < 10; ++q) o[q] = ajs[(int64_t)q * n_active + k];
-    correct_particle(d, i, t_next, o);
+    if (d.order == 4) correct_particle4(d, i, t_next, o);
+    else correct_particle(d, i, t_next, o);
 }
 
 // ---------------------------------------------------------------- start-up

@@ -38,7 +38,7 @@ class NbError(RuntimeError):
 class nb_params(C.Structure):
     _fields_ = [("eps", C.c_double), ("eta", C.c_double), ("eta_init", C.c_double),
                 ("dt_min", C.c_double), ("dt_max", C.c_double), ("precision", C.c_int32),
-                ("flags", C.c_uint32)]
+                ("flags", C.c_uint32), ("order", C.c_int32), ("reserved", C.c_int32)]
 
 
 STATE_FIELDS = ("m", "x", "v", "a", "j", "s", "c", "t", "dt", "pot")
@@ -237,7 +237,7 @@ class Simulation:
 
     def __init__(self, m, x, v, eps, eta=0.4, eta_init=0.01, dt_min=2.0 ** -20,
                  dt_max=2.0 ** -3, precision="fp64", offsets=None, device="cuda",
-                 keep_state=False, stream=None, time_eval=False):
+                 keep_state=False, stream=None, time_eval=False, order=6):
         import torch
         n = int(np.asarray(m).shape[0])
         self.n = n
@@ -254,7 +254,9 @@ class Simulation:
         self.params = nb_params(float(eps), float(eta), float(eta_init), float(dt_min),
                                 float(dt_max), PRECISIONS[precision] if isinstance(precision, str)
                                 else int(precision),
-                                (NB_INIT_KEEP_STATE if keep_state else 0) | (NB_TIME_EVAL if time_eval else 0))
+                                (NB_INIT_KEEP_STATE if keep_state else 0) | (NB_TIME_EVAL if time_eval else 0),
+                                int(order), 0)
+        self.order = int(order)
         self.stream = stream
         self._state = make_state(self.buf)
         torch.cuda.synchronize(self.device)

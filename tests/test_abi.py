@@ -54,6 +54,21 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu(libpath):
     # n = 0
     assert L.nb_init(ctypes.byref(ctx), ctypes.byref(p), 0, ctypes.byref(st), 1, None, None) == 1
     assert ctx.value is None
+    # integration order other than 4 / 6, and a non-zero reserved field
+    null_free = {f: 8 for f in nb.STATE_FIELDS}  # any non-NULL value: not dereferenced
+    st2 = nb.nb_state(**null_free)
+    p3 = nb.nb_params(1e-2, 0.4, 0.01, 2.0 ** -20, 2.0 ** -3, 0, 0, 5, 0)
+    assert L.nb_init(ctypes.byref(ctx), ctypes.byref(p3), 10, ctypes.byref(st2), 1, None, None) == 1
+    assert b"order" in L.nb_last_error(None)
+    p4 = nb.nb_params(1e-2, 0.4, 0.01, 2.0 ** -20, 2.0 ** -3, 0, 0, 4, 1)
+    assert L.nb_init(ctypes.byref(ctx), ctypes.byref(p4), 10, ctypes.byref(st2), 1, None, None) == 1
+    assert b"reserved" in L.nb_last_error(None)
+
+
+def test_params_layout_matches_header():
+    """nb_params: five doubles, then precision, flags, order, reserved."""
+    assert ctypes.sizeof(nb.nb_params) == 56
+    assert nb.nb_params.order.offset == 48
 
 
 def test_no_cpu_fallback_in_package():
