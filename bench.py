@@ -90,11 +90,11 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"nb_clocks_{os.getpid()}_{id(self)}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
@@ -365,9 +365,10 @@ def eval_case(args):
     nb.load()
     dev = torch.device("cuda", 0)
     m, x, v = ic.plummer(args.n, seed=SEED)
-    r = eval_rate(nb, torch, dev, m, x, v, args.precision, args.active, args.reps)
+    r = eval_rate(nb, torch, dev, m, x, v, args.precision, args.active, args.reps,
+                  order=args.order)
     print(json.dumps({"case": "eval", "precision": args.precision, "n": args.n,
-                      "active": args.active, **r,
+                      "active": args.active, "order": args.order, **r,
                       "gflops_79": r["interactions_per_s"] * FLOPS_PER_INTERACTION / 1e9}))
 
 
@@ -620,6 +621,56 @@ def order4_case(args):
     print(json.dumps(out))
 
 
+def energy_case(args):
+    """Energy per interaction: board power (nvidia-smi, every 200 ms) while the
+    all-active evaluation of the Plummer N=65536 system repeats for about
+    four seconds, times the CUDA-event time, over the interactions; FP64, EX
+    and FP32, 6th- and 4th-order pair terms."""
+    import torch
+    from paper_1812_00367_gb300 import build as nbbuild
+    from paper_1812_00367_gb300 import ic, nb
+    nbbuild.build()
+    nb.load()
+    dev = torch.device("cuda", 0)
+    m, x, v = ic.plummer(N, seed=SEED)
+    out = {"case": "energy", "n": N, "active": N, "seconds_target": args.energy_seconds}
+    stream = torch.cuda.current_stream(dev)
+    for prec in ("fp64", "ex", "fp32"):
+        for order in (6, 4):
+            sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX,
+                                precision=prec, keep_state=True, order=order)
+            sim.predict(0.0, out=False)
+            act = torch.arange(N, dtype=torch.int32, device=dev)
+            o = torch.empty((10, N), dtype=torch.float64, device=dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nb.nb_evaluate(sim.ctx, 0, act, N, o)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            reps = max(2, int(math.ceil(args.energy_seconds / (e0.elapsed_time(e1) * 1e-3))))
+            clocks = ClockSampler(0)
+            clocks.start()
+            time.sleep(0.3)
+            e0.record(stream)
+            for _ in range(reps):
+                nb.nb_evaluate(sim.ctx, 0, act, N, o)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            clk = clocks.stop()
+            sim.sync()
+            sim.close()
+            sec = e0.elapsed_time(e1) * 1e-3
+            inter = reps * N * (N - 1)
+            p = clk.get("power_w_median")
+            out[f"{prec}/order{order}"] = {
+                "interactions_per_s": inter / sec, "seconds": sec, "power_w_median": p,
+                "nj_per_interaction": None if not p else p * sec / inter * 1e9,
+                "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
+                "samples": clk.get("samples")}
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------ CPU oracle
 def _oracle_setup():
     from oracle import nb_oracle
@@ -700,7 +751,7 @@ def main():
     ap.add_argument("--slice", type=float, default=SLICE,
                     help="N-body time per step (a power of two dividing 0.25); shorter for profiling")
     ap.add_argument("--case", choices=["run", "eval", "batched", "config3", "merger", "config2-check",
-                                       "order4"],
+                                       "order4", "energy"],
                     default="run")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--batched-target", type=int, default=0,
@@ -716,11 +767,13 @@ def main():
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--active", type=int, default=N)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--energy-seconds", type=float, default=4.0)
+    ap.add_argument("--order", type=int, default=6, choices=[4, 6], help="--case eval only")
     args = ap.parse_args()
     if args.case != "run":
         {"eval": eval_case, "batched": batched_case, "config3": config3_case,
          "merger": merger_case, "config2-check": config2_check,
-         "order4": order4_case}[args.case](args)
+         "order4": order4_case, "energy": energy_case}[args.case](args)
         return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()

@@ -12,7 +12,11 @@
 namespace nb {
 
 // ---------------------------------------------------------------- constants
-constexpr int kTPB = 128;      // threads per evaluation CTA (4 warps)
+#ifndef NB_EVAL_TPB
+#define NB_EVAL_TPB 128       // threads per evaluation CTA (64, 128 or 256)
+#endif
+constexpr int kTPB = NB_EVAL_TPB;
+static_assert(kTPB == 64 || kTPB == 128 || kTPB == 256, "evaluation CTA: 64, 128 or 256 threads");
 constexpr int kTJ = 64;        // j-particles per shared-memory tile
 #ifndef NB_EVAL_STAGES
 #define NB_EVAL_STAGES 4
