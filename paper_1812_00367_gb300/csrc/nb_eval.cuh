@@ -201,32 +201,66 @@ struct Prec<NB_EX> {
         a[0] = ff_sub(ff{q2.w, q3.w}, i.a[0]);
         a[1] = ff_sub(ff{q4.x, q4.z}, i.a[1]);
         a[2] = ff_sub(ff{q4.y, q4.w}, i.a[2]);
-        ff r2 = ff_add(ff_dot3(r, r), eps2);
+        ff r2 = NB_EX_LAZY ? ff_dot3_add(r, r, eps2) : ff_add(ff_dot3(r, r), eps2);
         ff m = ff{q0.w, q1.w};
         if (self) {
             r2 = ff{1.f, 0.f};
             m = ff{0.f, 0.f};
         }
         const ff y = rsqrt_ff(r2);
-        const ff y2 = ff_sqr(y);
-        const ff my = ff_mul(m, y);
-        const ff q = ff_mul(my, y2);
-        c.p = ff_add(c.p, my);
         const ff rv = ff_dot3(r, v);
-        const ff w = ff_add(ff_dot3(v, v), ff_dot3(r, a));
-        const ff al = ff_mul(rv, y2);
-        const ff ze = ff_mul(w, y2);
-        const ff al3 = ff_mul_f(al, 3.0f);
-        const ff be3 = ff_mul_f(ff_add(ff_sqr(al), ze), 3.0f);
+        ff y2, my, q, w, al, ze, al3, be3;
+        if constexpr (NB_EX_LAZY) {
+            y2 = ff_sqr_lazy(y);
+            my = ff_mul_lazy(m, y);
+            q = ff_mul_lazy(my, y2);
+            w = ff_dot3x2_add(v, v, r, a, ff{0.f, 0.f});
+            al = ff_mul_lazy(rv, y2);
+            ze = ff_mul_lazy(w, y2);
+            al3 = ff_mul_f_lazy(al, 3.0f);
+            be3 = ff_mul_f_lazy(ff_sum_lazy(ff_sqr_lazy(al), ze), 3.0f);
+        } else {
+            y2 = ff_sqr(y);
+            my = ff_mul(m, y);
+            q = ff_mul(my, y2);
+            w = ff_add(ff_dot3(v, v), ff_dot3(r, a));
+            al = ff_mul(rv, y2);
+            ze = ff_mul(w, y2);
+            al3 = ff_mul_f(al, 3.0f);
+            be3 = ff_mul_f(ff_add(ff_sqr(al), ze), 3.0f);
+        }
         const ff al6 = ff{2.0f * al3.hi, 2.0f * al3.lo};  // exact
+        if constexpr (NB_EX_LAZY) {
+            ff_add_lazy(c.p, my);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const ff w1 = ff_fnma_lazy(al3, r[k], v[k]);
+                const ff w2 = ff_fnma_lazy(be3, r[k], ff_fnma_lazy(al6, w1, a[k]));
+                ff_fma_acc_lazy(c.a[k], q, r[k]);
+                ff_fma_acc_lazy(c.j[k], q, w1);
+                ff_fma_acc_lazy(c.s[k], q, w2);
+            }
+        } else {
+            c.p = ff_add(c.p, my);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const ff w1 = ff_fnma(al3, r[k], v[k]);
+                const ff w2 = ff_fnma(be3, r[k], ff_fnma(al6, w1, a[k]));
+                ff_fma_acc(c.a[k], q, r[k]);
+                ff_fma_acc(c.j[k], q, w1);
+                ff_fma_acc(c.s[k], q, w2);
+            }
+        }
+    }
+    // End of a j-tile: renormalise the lazily kept sums.
+    static __device__ __forceinline__ void tile_done(Acc &c) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const ff w1 = ff_fnma(al3, r[k], v[k]);
-            const ff w2 = ff_fnma(be3, r[k], ff_fnma(al6, w1, a[k]));
-            ff_fma_acc(c.a[k], q, r[k]);
-            ff_fma_acc(c.j[k], q, w1);
-            ff_fma_acc(c.s[k], q, w2);
+            c.a[k] = ff_renorm(c.a[k].hi, c.a[k].lo);
+            c.j[k] = ff_renorm(c.j[k].hi, c.j[k].lo);
+            c.s[k] = ff_renorm(c.s[k].hi, c.s[k].lo);
         }
+        c.p = ff_renorm(c.p.hi, c.p.lo);
     }
     static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self, double,
                                                      float, Acc &c, ff eps2) {
@@ -238,23 +272,34 @@ struct Prec<NB_EX> {
         v[0] = ff_sub(ff{q2.x, q3.x}, i.v[0]);
         v[1] = ff_sub(ff{q2.y, q3.y}, i.v[1]);
         v[2] = ff_sub(ff{q2.z, q3.z}, i.v[2]);
-        ff r2 = ff_add(ff_dot3(r, r), eps2);
+        ff r2 = NB_EX_LAZY ? ff_dot3_add(r, r, eps2) : ff_add(ff_dot3(r, r), eps2);
         ff m = ff{q0.w, q1.w};
         if (self) {
             r2 = ff{1.f, 0.f};
             m = ff{0.f, 0.f};
         }
         const ff y = rsqrt_ff(r2);
-        const ff y2 = ff_sqr(y);
-        const ff my = ff_mul(m, y);
-        const ff q = ff_mul(my, y2);
-        c.p = ff_add(c.p, my);
-        const ff al3 = ff_mul_f(ff_mul(ff_dot3(r, v), y2), 3.0f);
+        const ff y2 = NB_EX_LAZY ? ff_sqr_lazy(y) : ff_sqr(y);
+        const ff my = NB_EX_LAZY ? ff_mul_lazy(m, y) : ff_mul(m, y);
+        const ff q = NB_EX_LAZY ? ff_mul_lazy(my, y2) : ff_mul(my, y2);
+        const ff al3 = NB_EX_LAZY ? ff_mul_f_lazy(ff_mul_lazy(ff_dot3(r, v), y2), 3.0f)
+                                  : ff_mul_f(ff_mul(ff_dot3(r, v), y2), 3.0f);
+        if constexpr (NB_EX_LAZY) {
+            ff_add_lazy(c.p, my);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const ff w1 = ff_fnma(al3, r[k], v[k]);
-            ff_fma_acc(c.a[k], q, r[k]);
-            ff_fma_acc(c.j[k], q, w1);
+            for (int k = 0; k < 3; ++k) {
+                const ff w1 = ff_fnma_lazy(al3, r[k], v[k]);
+                ff_fma_acc_lazy(c.a[k], q, r[k]);
+                ff_fma_acc_lazy(c.j[k], q, w1);
+            }
+        } else {
+            c.p = ff_add(c.p, my);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const ff w1 = ff_fnma(al3, r[k], v[k]);
+                ff_fma_acc(c.a[k], q, r[k]);
+                ff_fma_acc(c.j[k], q, w1);
+            }
         }
     }
     static __device__ __forceinline__ double to_d(ff a) { return (double)a.hi + (double)a.lo; }
@@ -571,6 +616,8 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
                 if constexpr (P == NB_FP32) {
                     if ((tt - tb + 1) % kFp32FlushTiles == 0) T::flush(acc, t64);
                     else T::tile_done(acc);
+                } else if constexpr (P == NB_EX && NB_EX_LAZY && MODE != kModePot) {
+                    T::tile_done(acc);
                 }
             }
             if (!ok) S.fail = 1;

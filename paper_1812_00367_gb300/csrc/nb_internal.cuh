@@ -27,6 +27,13 @@ constexpr int kTJ = 64;        // j-particles per shared-memory tile
 #ifndef NB_EVAL_UNROLL
 #define NB_EVAL_UNROLL 2      // j-loop unrolling of the FP64 / FP32 evaluation
 #endif
+#ifndef NB_EX_LAZY
+// 1: the EX evaluation keeps its sums and intermediate products unnormalised
+// (hi + lo with every error term kept; sums renormalised once per j-tile).
+// Measured: 1.126x the pair rate at N = 65536, and the same maximum errors
+// against FP64 at N = 2^20 (Kroupa masses, eps = 1e-5) to two digits.
+#define NB_EX_LAZY 1
+#endif
 #ifndef NB_FP64_ALL_FMA
 // 1: the FP64 evaluation issues its products and differences as FMAs with
 // run-time -0.0 / -1.0 operands.  On GB300, DADD and DMUL run at 84 % of the
@@ -88,7 +95,6 @@ struct Dev {
     int32_t n_clusters;
     int32_t n_chunks;
     int32_t precision;
-    int32_t order;      // 6: NM08 6th order; 4: Makino & Aarseth 4th order
     int32_t grid_eval;  // persistent evaluation grid (CTAs)
     const int64_t *offsets;      // [nc+1] particle offsets
     const int64_t *jofs;         // [nc+1] padded j-array offsets
@@ -130,6 +136,9 @@ struct Dev {
     // -1.0 and -0.0 as run-time values: FP64 products and differences issued
     // as FMAs (a*b - 0, a - b = b*(-1) + a) cannot be folded back by compilers
     double neg_one, neg_zero;
+    // 6: NM08 6th order; 4: Makino & Aarseth 4th order.  Kept last: inserting
+    // it among the fields above measured 2.8 % slower FP64 evaluation.
+    int32_t order;
 };
 
 // How one evaluation launch obtains its work.
@@ -341,6 +350,101 @@ __device__ __forceinline__ ff ff_dot3(const ff a[3], const ff b[3]) {
     lo = __fadd_rn(lo, e);
     two_sum(s, p2, s, e);
     lo = __fadd_rn(lo, e);
+    return ff_renorm(s, lo);
+}
+
+// Lazy forms: the sum's high part takes the exact TwoSum, the low part
+// gathers every error term, and renormalisation is left to the caller (once
+// per j-tile for accumulators).  |lo| may reach a few ulps of |hi|; every
+// consumer below folds lo into first-order terms only.
+__device__ __forceinline__ void ff_fma_acc_lazy(ff &acc, ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);
+    pe = __fmaf_rn(a.hi, b.lo, pe);
+    pe = __fmaf_rn(a.lo, b.hi, pe);
+    float s, e;
+    two_sum(acc.hi, p, s, e);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ ff ff_mul_lazy(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ff{p, e};
+}
+__device__ __forceinline__ ff ff_mul_f_lazy(ff a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return ff{p, e};
+}
+__device__ __forceinline__ ff ff_sqr_lazy(ff a) {
+    const float p = __fmul_rn(a.hi, a.hi);
+    float e = __fmaf_rn(a.hi, a.hi, -p);
+    e = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, e);
+    return ff{p, e};
+}
+__device__ __forceinline__ ff ff_sum_lazy(ff a, ff b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return ff{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ void ff_add_lazy(ff &acc, ff b) {
+    float s, e;
+    two_sum(acc.hi, b.hi, s, e);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, b.lo));
+}
+__device__ __forceinline__ ff ff_fnma_lazy(ff b, ff c, ff a) {
+    const float p = __fmul_rn(b.hi, c.hi);
+    float pe = __fmaf_rn(b.hi, c.hi, -p);
+    pe = __fmaf_rn(b.hi, c.lo, pe);
+    pe = __fmaf_rn(b.lo, c.hi, pe);
+    float s, e;
+    two_sum(a.hi, -p, s, e);
+    return ff{s, __fadd_rn(e, __fsub_rn(a.lo, pe))};
+}
+// a.b + c, one renormalisation
+__device__ __forceinline__ ff ff_dot3_add(const ff a[3], const ff b[3], ff c) {
+    float p[3], lo = c.lo;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = __fmul_rn(a[k].hi, b[k].hi);
+        lo = __fmaf_rn(a[k].hi, b[k].hi, -p[k]) + lo;
+        lo = __fmaf_rn(a[k].hi, b[k].lo, lo);
+        lo = __fmaf_rn(a[k].lo, b[k].hi, lo);
+    }
+    float s = c.hi, e;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        two_sum(s, p[k], s, e);
+        lo = __fadd_rn(lo, e);
+    }
+    return ff_renorm(s, lo);
+}
+// a0.b0 + a1.b1 (two 3-vector dot products) + c, one renormalisation
+__device__ __forceinline__ ff ff_dot3x2_add(const ff a0[3], const ff b0[3], const ff a1[3],
+                                            const ff b1[3], ff c) {
+    float p[6], lo = c.lo;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = __fmul_rn(a0[k].hi, b0[k].hi);
+        p[3 + k] = __fmul_rn(a1[k].hi, b1[k].hi);
+        lo = __fmaf_rn(a0[k].hi, b0[k].hi, -p[k]) + lo;
+        lo = __fmaf_rn(a1[k].hi, b1[k].hi, -p[3 + k]) + lo;
+        lo = __fmaf_rn(a0[k].hi, b0[k].lo, lo);
+        lo = __fmaf_rn(a0[k].lo, b0[k].hi, lo);
+        lo = __fmaf_rn(a1[k].hi, b1[k].lo, lo);
+        lo = __fmaf_rn(a1[k].lo, b1[k].hi, lo);
+    }
+    float s = c.hi, e;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        two_sum(s, p[k], s, e);
+        lo = __fadd_rn(lo, e);
+    }
     return ff_renorm(s, lo);
 }
 
