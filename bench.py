@@ -49,7 +49,8 @@ WORKLOAD = (f"Plummer N={N}, equal masses, Henon units, eps={EPS:g}, block steps
 # launch of one ncu capture of this workload (summary and command in
 # profiles/).  It holds for the kernel sources it was taken on (SHA-256 of
 # EVAL_SOURCES below); after any change to them it is reported as null.
-EVAL_TRAFFIC = {"bytes_per_launch": None, "launches": None, "sources_sha256": None}
+EVAL_TRAFFIC = {"bytes_per_launch": 6480502, "launches": 1520,
+                "sources_sha256": "c8345926a9dac63f35c7fcfd2e09957a27f7fa7d367a4f68007184798d3cff4d"}
 EVAL_SOURCES = ("nb_eval.cuh", "nb_eval_fp64.cu", "nb_step.cuh", "nb_internal.cuh")
 
 
@@ -581,6 +582,54 @@ def merger_case(args):
     print(json.dumps(out))
 
 
+def histogram_case(args):
+    """Configuration 2 (Plummer N=65536, eps 1e-4, eta 0.4, block steps)
+    from start-up to t = 0.25 one block step at a time, FP64: the active-set
+    histogram in floor(log2 A) buckets with each bucket's block steps,
+    interactions, evaluation time (CUDA events around each evaluation launch)
+    and interactions/s; the energy error at the end."""
+    import torch
+    import tempfile
+    from paper_1812_00367_gb300 import build as nbbuild
+    from paper_1812_00367_gb300 import ic, nb
+    nbbuild.build()
+    nb.load()
+    m, x, v = ic.plummer(N, seed=SEED)
+    sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX,
+                        precision="fp64", time_eval=True)
+    if not args.no_autotune:
+        sim.autotune(os.path.join(tempfile.mkdtemp(prefix="nbtune_"), "fp64.txt"))
+    e0 = sum(sim.energy(0.0)[:2])
+    buckets = {}
+    tn, steps = 0.0, 0
+    while tn < T_END:
+        c0 = sim.counters()["eval_ms"]
+        tn, na = sim.step()
+        ms = sim.counters()["eval_ms"] - c0
+        b = int(math.floor(math.log2(max(na, 1))))
+        r = buckets.setdefault(b, [0, 0.0, 0.0, {}])
+        r[0] += 1
+        r[1] += float(na) * (N - 1)
+        r[2] += ms
+        r[3][na] = r[3].get(na, 0) + 1
+        steps += 1
+    e1 = sum(sim.energy(T_END)[:2])
+    sim.close()
+    rows = [{"log2_active": b, "block_steps": r[0], "interactions": r[1], "eval_ms": r[2],
+             "interactions_per_s": r[1] / (r[2] * 1e-3) if r[2] > 0 else None,
+             "share_of_interactions": None,
+             "most_common_active": sorted(r[3].items(), key=lambda kv: -kv[1])[:4]}
+            for b, r in sorted(buckets.items())]
+    tot_i = sum(r["interactions"] for r in rows)
+    tot_ms = sum(r["eval_ms"] for r in rows)
+    for r in rows:
+        r["share_of_interactions"] = r["interactions"] / tot_i
+    print(json.dumps({"case": "histogram", "n": N, "t_end": T_END, "block_steps": steps,
+                      "interactions": tot_i, "eval_seconds": tot_ms * 1e-3,
+                      "eval_interactions_per_s": tot_i / (tot_ms * 1e-3),
+                      "rel_energy_error": abs(e1 - e0) / abs(e0), "buckets": rows}))
+
+
 ETA4 = 0.02
 
 
@@ -751,7 +800,7 @@ def main():
     ap.add_argument("--slice", type=float, default=SLICE,
                     help="N-body time per step (a power of two dividing 0.25); shorter for profiling")
     ap.add_argument("--case", choices=["run", "eval", "batched", "config3", "merger", "config2-check",
-                                       "order4", "energy"],
+                                       "order4", "energy", "histogram"],
                     default="run")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--batched-target", type=int, default=0,
@@ -773,7 +822,8 @@ def main():
     if args.case != "run":
         {"eval": eval_case, "batched": batched_case, "config3": config3_case,
          "merger": merger_case, "config2-check": config2_check,
-         "order4": order4_case, "energy": energy_case}[args.case](args)
+         "order4": order4_case, "energy": energy_case,
+         "histogram": histogram_case}[args.case](args)
         return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
