@@ -64,6 +64,11 @@ typedef enum {
                                  (resume); skip the start-up evaluations */
 #define NB_TIME_EVAL 2u       /* record CUDA events around every evaluation
                                  launch of nb_step / nb_run (nb_counters.eval_ms) */
+#define NB_NO_STREAMK 4u      /* split one-cluster evaluations into j-range items
+                                 as in a batch instead of equal stream-K ranges
+                                 per CTA: a cluster's results are then
+                                 bit-identical alone and in a batch that uses
+                                 the same plan table */
 
 typedef struct {
     double eps;      /* Plummer softening length; pairs use |r|^2 + eps^2 */

@@ -212,13 +212,20 @@ nb_status set_tend(nb_ctx *ctx, double t_end) {
 }
 
 // Plan a direct (host-driven) evaluation of n_active particles of one cluster.
-void plan_direct(const nb_ctx *ctx, int cluster, int32_t n_active, int &gl, int &split, int &tiles) {
+void plan_direct(const nb_ctx *ctx, int cluster, int32_t n_active, int &gl, int &split, int &tiles,
+                 int &streamk) {
     const int b = 31 - __builtin_clz((unsigned)std::max(n_active, 1));
     const PlanEntry e = ctx->table[b];
     gl = e.gl;
     tiles = (int)cdiv(n_active, kTPB / gl);
     const int64_t ncl = ctx->h_offsets[cluster + 1] - ctx->h_offsets[cluster];
     const int64_t ntj = cdiv(ncl, kTJ);
+    streamk = !(ctx->p.flags & NB_NO_STREAMK) &&
+              sk_use(tiles, kTPB / gl, ntj, ctx->grid_eval, ctx->d.partial_cap) ? 1 : 0;
+    if (streamk) {
+        split = 1;
+        return;
+    }
     int64_t S = choose_split(tiles, ntj, e.target_items, ctx->grid_eval);
     const int64_t per_item = 10LL * (kTPB / gl);  // partial doubles per item
     if (S > 1 && (int64_t)tiles * S * per_item > ctx->d.partial_cap)
@@ -227,7 +234,7 @@ void plan_direct(const nb_ctx *ctx, int cluster, int32_t n_active, int &gl, int 
 }
 
 nb_status eval_direct(nb_ctx *ctx, int cluster, const int32_t *active, int32_t n_active, double *out,
-                      int gl, int split, int tiles) {
+                      int gl, int split, int tiles, int streamk) {
     EvalLaunch L{};
     L.direct = 1;
     L.cluster = cluster;
@@ -237,8 +244,10 @@ nb_status eval_direct(nb_ctx *ctx, int cluster, const int32_t *active, int32_t n
     L.tiles = tiles;
     L.active = active;
     L.out = out;
+    L.streamk = streamk;
     const int64_t items = (int64_t)tiles * split;
-    const int grid = (int)std::min<int64_t>(items, ctx->grid_eval);
+    // stream-K ranges were cut for the whole persistent grid
+    const int grid = streamk ? ctx->grid_eval : (int)std::min<int64_t>(items, ctx->grid_eval);
     NB_CU(ctx, launch_eval(ctx->d, ctx->d.order == 4 ? kModeOut4 : kModeOut, L, grid, ctx->stream));
     return NB_OK;
 }
@@ -372,6 +381,7 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     d.n_chunks = n_chunks;
     d.precision = p->precision;
     d.order = p->order == 4 ? 4 : 6;
+    d.streamk_off = (p->flags & NB_NO_STREAMK) ? 1 : 0;
     d.m = st->m; d.x = st->x; d.v = st->v; d.a = st->a; d.j = st->j; d.s = st->s; d.c = st->c;
     d.t = st->t; d.dt = st->dt; d.pot = st->pot;
     d.eps2 = p->eps * p->eps;
@@ -524,9 +534,9 @@ nb_status nb_evaluate(nb_ctx *ctx, int32_t cluster, const int32_t *active, int32
     if (n_active < 0 || n_active > ncl) return fail(ctx, NB_EINVAL, "nb_evaluate: n_active out of range");
     if (n_active == 0) return NB_OK;
     if (!active || !out_ajs) return fail(ctx, NB_EINVAL, "nb_evaluate: NULL pointer");
-    int gl, split, tiles;
-    plan_direct(ctx, cluster, n_active, gl, split, tiles);
-    return eval_direct(ctx, cluster, active, n_active, out_ajs, gl, split, tiles);
+    int gl, split, tiles, streamk;
+    plan_direct(ctx, cluster, n_active, gl, split, tiles, streamk);
+    return eval_direct(ctx, cluster, active, n_active, out_ajs, gl, split, tiles, streamk);
 }
 
 nb_status nb_correct_and_timestep(nb_ctx *ctx, int32_t cluster, const int32_t *active,
@@ -781,12 +791,12 @@ nb_status nb_autotune(nb_ctx *ctx, const char *cache_path) {
             for (int64_t tg : targets) {
                 if (tg > ctx->cap_items / 2) continue;
                 ctx->table[b] = PlanEntry{gl, (int32_t)tg};
-                int g2, sp, tl;
-                plan_direct(ctx, cmax, A, g2, sp, tl);
+                int g2, sp, tl, skm;
+                plan_direct(ctx, cmax, A, g2, sp, tl, skm);
                 float ms_best = 1e30f;
                 for (int rep = 0; rep < reps; ++rep) {
                     cudaEventRecord(e0, ctx->stream);
-                    st = eval_direct(ctx, cmax, d_act, A, d_out, g2, sp, tl);
+                    st = eval_direct(ctx, cmax, d_act, A, d_out, g2, sp, tl, skm);
                     cudaEventRecord(e1, ctx->stream);
                     if (st != NB_OK) break;
                     e = cudaEventSynchronize(e1);

@@ -493,6 +493,13 @@ __device__ __forceinline__ int64_t next_item_of(const EvalLaunch &L, const Dev &
     return S.next_item;
 }
 
+// Units of a stream-K launch (one cluster): i-tiles x j-tiles.
+__device__ __forceinline__ int64_t sk_units(const Dev &d, const EvalLaunch &L) {
+    const int c = L.direct ? L.cluster : 0;
+    const int64_t tiles = L.direct ? L.tiles : d.plan[0].tiles;
+    return tiles * cdiv(d.offsets[c + 1] - d.offsets[c], kTJ);
+}
+
 template <int P, int MODE>
 __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, const EvalLaunch L) {
     using T = Prec<P>;
@@ -518,38 +525,58 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
     uint32_t phase = 0;   // bit s: parity of stage s
     uint32_t pending = 0; // bit s: a copy into stage s is in flight
 
-    // Items: direct launches (equal-cost items of one cluster) take a static
-    // round robin; planned launches fetch items dynamically, since clusters of
-    // a batch give items of unequal cost.  Either way an item's arithmetic and
-    // the split-order reduction do not depend on the CTA that runs it.
-    int64_t item = blockIdx.x;
-    if (!L.direct) {
+    // Work: a stream-K launch (one cluster) gives CTA k the unit range
+    // [U k / G, U (k+1) / G) and walks it piece by piece (one piece per i-tile
+    // it touches).  Otherwise work items (cluster, i-tile, split index):
+    // direct launches (equal-cost items of one cluster) take a static round
+    // robin; planned launches fetch items dynamically, since clusters of a
+    // batch give items of unequal cost.  Either way a piece's arithmetic and
+    // the reduction order do not depend on the CTA that runs it.
+    const bool sk = L.direct ? L.streamk != 0 : (d.n_clusters == 1 && d.plan[0].streamk != 0);
+    // stream-K: `item` walks this CTA's unit range and `item_end` closes it
+    int64_t item = blockIdx.x, item_end = n_items;
+    if (sk) {
+        item = sk_begin(sk_units(d, L), gridDim.x, blockIdx.x);
+        item_end = sk_begin(sk_units(d, L), gridDim.x, blockIdx.x + 1);
+    } else if (!L.direct) {
         if (tid == 0) S.next_item = (long long)atomicAdd(d.item_ctr, 1ull);
         __syncthreads();
         item = S.next_item;
     }
-    for (; item < n_items;) {
+    for (; item < item_end;) {
         int c, gl, split, A;
         int64_t item0, tile0, pslot0;
         if (L.direct) {
             c = L.cluster; gl = L.gl; split = L.split; A = L.n_active; item0 = 0; tile0 = 0;
             pslot0 = 0;
         } else {
-            c = find_cluster(d.plan, d.n_clusters, item);
+            c = sk ? 0 : find_cluster(d.plan, d.n_clusters, item);
             const ClusterPlan pl = d.plan[c];
             gl = pl.gl; split = pl.split; A = pl.active; item0 = pl.item0; tile0 = pl.tile0;
             pslot0 = pl.pslot0;
         }
-        const int64_t local = item - item0;
-        const int tile = (int)(local / split);
-        const int sidx = (int)(local % split);
+        const int64_t nc = d.offsets[c + 1] - d.offsets[c];
+        const int64_t ntj = cdiv(nc, kTJ);
+        int64_t local, tb, te;
+        int tile;
+        if (sk) {
+            local = 0;
+            tile = (int)(item / ntj);
+            tb = item - (int64_t)tile * ntj;
+            te = min(ntj, tb + (item_end - item));
+        } else {
+            local = item - item0;
+            tile = (int)(local / split);
+            const int sidx = (int)(local % split);
+            tb = ntj * sidx / split;
+            te = ntj * (sidx + 1) / split;
+        }
         const int Ti = kTPB / gl;
         const int ilane = tid / gl;
         const int jsub = tid % gl;
         const int iloc = tile * Ti + ilane;
         const bool valid = iloc < A;
         const int64_t off = d.offsets[c];
-        const int64_t nc = d.offsets[c + 1] - off;
         const J *jc = jall + d.jofs[c];
         int64_t gi = off;
         bool bad_index = false;
@@ -572,9 +599,6 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
 #pragma unroll
         for (int q = 0; q < 10; ++q) t64[q] = 0.0;
 
-        const int64_t ntj = cdiv(nc, kTJ);
-        const int64_t tb = ntj * sidx / split;
-        const int64_t te = ntj * (sidx + 1) / split;
         const bool warp_active = __any_sync(0xffffffffu, valid);
 
         // prologue: fill the ring
@@ -651,12 +675,37 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
             for (int q = 0; q < 10; ++q) o[q] += __shfl_xor_sync(0xffffffffu, o[q], w);
         }
 
-        if (split == 1) {
+        // pieces of this i-tile: split items, or the CTAs whose ranges meet it
+        int npieces = split;
+        int64_t sk_first = 0, sk_maxp = 0, sk_loc0 = 0;
+        if (sk) {
+            const int64_t U = sk_units(d, L);
+            sk_first = sk_owner(U, gridDim.x, (int64_t)tile * ntj);
+            npieces = (int)(sk_owner(U, gridDim.x, (int64_t)(tile + 1) * ntj - 1) - sk_first + 1);
+            sk_maxp = sk_max_pieces(U, gridDim.x, ntj);
+            // the first piece's CTA may have started in an earlier i-tile; the
+            // others start inside this one (their local tile index is 0)
+            sk_loc0 = tile - sk_begin(U, gridDim.x, sk_first) / ntj;
+        }
+        // partial-sum slot (doubles) of piece s of this tile: CTA k keeps one
+        // slot per i-tile its range touches
+        auto piece_slot = [&](int64_t s) -> int64_t {
+            if (sk) return ((sk_first + s) * sk_maxp + (s == 0 ? sk_loc0 : 0)) * (10 * Ti);
+            return pslot0 + ((int64_t)tile * split + s) * (10 * Ti);
+        };
+        if (npieces == 1) {
             if (valid && jsub == 0 && !bad_index) finalize_one<P, MODE>(d, L, c, gi, iloc, o);
-            item = next_item_of<P>(L, d, S, item);
+            if (sk) {
+                item += te - tb;
+                __syncthreads();
+            } else {
+                item = next_item_of<P>(L, d, S, item);
+            }
             continue;
         }
-        double *part = d.partial + pslot0 + local * (int64_t)(10 * Ti);
+        // this CTA's piece of the tile
+        double *part = d.partial + (sk ? piece_slot((int64_t)blockIdx.x - sk_first)
+                                       : pslot0 + local * (int64_t)(10 * Ti));
         if (jsub == 0) {
 #pragma unroll
             for (int q = 0; q < 10; ++q) part[q * Ti + ilane] = o[q];
@@ -665,27 +714,31 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
         __syncthreads();
         if (tid == 0) {
             const int prev = atomicAdd(&d.tile_cnt[tile0 + tile], 1);
-            S.flag = (prev == split - 1);
+            S.flag = (prev == npieces - 1);
         }
         __syncthreads();
         if (S.flag) {
-            // Last CTA of this i-tile: add the split partials of every (i, q)
-            // pair in two fixed-order levels.  Level 1: thread (p, r) sums the
-            // r-th contiguous group of splits of pair p in split order; level 2
-            // adds the R group sums in group order.  The order depends only on
-            // (split, valid i count), so results are reproducible.
+            // Last CTA of this i-tile: add the partials of its pieces for every
+            // (i, q) pair in two fixed-order levels.  Level 1: thread (p, r)
+            // sums the r-th contiguous group of pieces of pair p in piece order;
+            // level 2 adds the R group sums in group order.  The order depends
+            // only on (pieces, valid i count), so results are reproducible.
             __threadfence();
             const int nv = min(Ti, A - tile * Ti);     // valid i in this tile
             const int npair = nv * 10;
             const int R = max(1, kTPB / npair);
-            const double *base = d.partial + pslot0 + (int64_t)tile * split * (10 * Ti);
             for (int w = tid; w < npair * R; w += kTPB) {
                 const int p = w % npair, r = w / npair;
                 const int q = p / nv, il = p % nv;
-                const int s0 = (int)((int64_t)split * r / R), s1 = (int)((int64_t)split * (r + 1) / R);
+                const int s0 = (int)((int64_t)npieces * r / R), s1 = (int)((int64_t)npieces * (r + 1) / R);
                 double acc = 0.0;
+                if (sk) {
+                    for (int sp = s0; sp < s1; ++sp) acc += __ldcg(d.partial + piece_slot(sp) + q * Ti + il);
+                } else {
+                    const double *base = d.partial + piece_slot(0);
 #pragma unroll 4
-                for (int sp = s0; sp < s1; ++sp) acc += __ldcg(base + (int64_t)sp * (10 * Ti) + q * Ti + il);
+                    for (int sp = s0; sp < s1; ++sp) acc += __ldcg(base + (int64_t)sp * (10 * Ti) + q * Ti + il);
+                }
                 S.red[r * npair + p] = acc;
             }
             __syncthreads();
@@ -707,7 +760,8 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
             if (tid == 0) d.tile_cnt[tile0 + tile] = 0;
         }
         __syncthreads();
-        item = next_item_of<P>(L, d, S, item);
+        if (sk) item += te - tb;
+        else item = next_item_of<P>(L, d, S, item);
     }
 }
 

@@ -82,6 +82,8 @@ struct ClusterPlan {
     int64_t item0;  // first work item of the cluster
     int64_t tile0;  // first i-tile of the cluster (counter index)
     int64_t pslot0; // first partial-sum double (only clusters with split > 1 use them)
+    int32_t streamk; // 1: single-cluster launch split stream-K style (split unused)
+    int32_t pad_;
 };
 
 struct PlanEntry {  // per active-set bucket
@@ -139,6 +141,7 @@ struct Dev {
     // 6: NM08 6th order; 4: Makino & Aarseth 4th order.  Kept last: inserting
     // it among the fields above measured 2.8 % slower FP64 evaluation.
     int32_t order;
+    int32_t streamk_off;  // NB_NO_STREAMK
 };
 
 // How one evaluation launch obtains its work.
@@ -152,6 +155,7 @@ struct EvalLaunch {
     int32_t identity;   // active list is 0..A-1 of the cluster (init, energy)
     const int32_t *active;  // direct mode list (global indices)
     double *out;        // direct mode output [10][n_active]
+    int32_t streamk;    // direct mode: stream-K ranges instead of split items
 };
 
 // Out/Step/Init1/Init2: 6th-order pair terms (a, jerk, snap); the *4 modes
@@ -166,6 +170,38 @@ constexpr bool is_order4_mode(int mode) { return mode >= kModeOut4; }
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 constexpr int kMinTilesPerItem = 4;  // a j-range holds at least 4 x 64 j
+
+// Stream-K decomposition of a single cluster's evaluation.  Its work is
+// U = tiles x ntj units (one i-tile against one j-tile, all of equal cost);
+// CTA k of G takes the contiguous unit range [U k / G, U (k+1) / G), so every
+// CTA (and every SM) gets the same work to within one unit.  A range splits
+// at i-tile boundaries into pieces; an i-tile covered by several CTAs gets one
+// partial sum per CTA, added in CTA order by the last one to finish.
+#ifndef NB_STREAMK
+#define NB_STREAMK 1
+#endif
+#ifndef NB_STREAMK_MIN_UNITS
+#define NB_STREAMK_MIN_UNITS 4
+#endif
+constexpr int kStreamKMinUnits = NB_STREAMK_MIN_UNITS;  // units per CTA below which splits are used
+__host__ __device__ inline int64_t sk_begin(int64_t U, int64_t G, int64_t k) { return U * k / G; }
+// CTA whose range holds unit p (the largest k with sk_begin(k) <= p; U >= G)
+__host__ __device__ inline int64_t sk_owner(int64_t U, int64_t G, int64_t p) {
+    return ((p + 1) * G + U - 1) / U - 1;
+}
+// most i-tiles one CTA's range can touch
+__host__ __device__ inline int64_t sk_max_pieces(int64_t U, int64_t G, int64_t ntj) {
+    return (cdiv(U, G) - 1) / ntj + 2;
+}
+// whether a launch of `tiles` i-tiles of Ti i's over ntj j-tiles on G CTAs
+// runs stream-K: enough units per CTA, partial sums within the scratch
+__host__ __device__ inline bool sk_use(int64_t tiles, int64_t Ti, int64_t ntj, int64_t G,
+                                       int64_t partial_cap) {
+    if (!NB_STREAMK || tiles <= 0) return false;
+    const int64_t U = tiles * ntj;
+    if (U < kStreamKMinUnits * G) return false;
+    return G * sk_max_pieces(U, G, ntj) * 10 * Ti <= partial_cap;
+}
 
 // Number of j-ranges (split S) for `tiles` i-tiles over a cluster of `ntj`
 // j-tiles.  Start from the bucket's target item count; keep at least

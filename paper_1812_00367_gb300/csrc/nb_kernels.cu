@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan(const Dev d, int mode_init, i
         double inter = 0.0, busy = 0.0;
         for (int base = 0; base < d.n_clusters; base += (int)blockDim.x) {
             const int c = base + tid;
-            ClusterPlan pl{1, 1, 0, 0, 0, 0, 0};
+            ClusterPlan pl{1, 1, 0, 0, 0, 0, 0, 0, 0};
             long long items = 0, tiles = 0;
             double my_inter = 0.0;
             if (c < d.n_clusters) {
@@ -154,10 +154,17 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan(const Dev d, int mode_init, i
                     const PlanEntry e = d.table[31 - __clz(A)];
                     tiles = cdiv(A, kTPB / e.gl);
                     const long long ntj = cdiv(ncl, kTJ);
-                    const long long S =
-                        fallback ? 1 : choose_split(tiles, ntj, e.target_items, d.grid_eval);
-                    items = tiles * S;
-                    pl = ClusterPlan{e.gl, (int)S, (int)tiles, A, 0, 0, 0};
+                    if (d.n_clusters == 1 && !d.streamk_off &&
+                        sk_use(tiles, kTPB / e.gl, ntj, d.grid_eval, d.partial_cap)) {
+                        // one cluster, enough work: stream-K ranges (one "item")
+                        items = 1;
+                        pl = ClusterPlan{e.gl, 1, (int)tiles, A, 0, 0, 0, 1, 0};
+                    } else {
+                        const long long S =
+                            fallback ? 1 : choose_split(tiles, ntj, e.target_items, d.grid_eval);
+                        items = tiles * S;
+                        pl = ClusterPlan{e.gl, (int)S, (int)tiles, A, 0, 0, 0, 0, 0};
+                    }
                     my_inter = (double)A * (double)(ncl - 1);
                 }
             }

@@ -25,6 +25,7 @@ NB_FP64, NB_EX, NB_FP32 = 0, 1, 2
 PRECISIONS = {"fp64": NB_FP64, "ex": NB_EX, "fp32": NB_FP32}
 NB_INIT_KEEP_STATE = 1
 NB_TIME_EVAL = 2
+NB_NO_STREAMK = 4
 STATUS = {0: "NB_OK", 1: "NB_EINVAL", 2: "NB_ENOMEM", 3: "NB_ECUDA", 4: "NB_ENONFINITE",
           5: "NB_EDTUNDERFLOW", 6: "NB_ETIMEOUT", 7: "NB_ESTATE"}
 
@@ -237,7 +238,7 @@ class Simulation:
 
     def __init__(self, m, x, v, eps, eta=0.4, eta_init=0.01, dt_min=2.0 ** -20,
                  dt_max=2.0 ** -3, precision="fp64", offsets=None, device="cuda",
-                 keep_state=False, stream=None, time_eval=False, order=6):
+                 keep_state=False, stream=None, time_eval=False, order=6, streamk=True):
         import torch
         n = int(np.asarray(m).shape[0])
         self.n = n
@@ -254,7 +255,8 @@ class Simulation:
         self.params = nb_params(float(eps), float(eta), float(eta_init), float(dt_min),
                                 float(dt_max), PRECISIONS[precision] if isinstance(precision, str)
                                 else int(precision),
-                                (NB_INIT_KEEP_STATE if keep_state else 0) | (NB_TIME_EVAL if time_eval else 0),
+                                (NB_INIT_KEEP_STATE if keep_state else 0) | (NB_TIME_EVAL if time_eval else 0)
+                                | (0 if streamk else NB_NO_STREAMK),
                                 int(order), 0)
         self.order = int(order)
         self.stream = stream

@@ -52,7 +52,7 @@ def test_batched_equals_single_bit_for_bit(nb, tmp_path, precision):
     for c, n_c in enumerate(sizes):
         lo, hi = batch.offsets[c], batch.offsets[c + 1]
         s1 = nb.Simulation(batch.m[lo:hi], batch.x[lo:hi], batch.v[lo:hi], eps=1e-3,
-                           precision=precision, keep_state=True)
+                           precision=precision, keep_state=True, streamk=False)
         s1.autotune(table)
         s1.set_state_numpy({f: st0[f][lo:hi] for f in st0})
         s1.run(t_end)

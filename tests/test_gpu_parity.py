@@ -109,6 +109,40 @@ def test_evaluate_parity(nb, oracle, precision, n):
     sim.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "ex", "fp32"])
+@pytest.mark.parametrize("n", [8192, 10007])
+def test_evaluate_streamk_parity(nb, oracle, precision, n):
+    """Large one-cluster evaluations run as stream-K ranges (each CTA an equal
+    share of i-tile x j-tile units, pieces summed in CTA order): oracle parity,
+    agreement with the split-item plan to rounding, bit-for-bit repeats."""
+    eps = 1e-4
+    m, x, v, a = _plummer_state(oracle, n, seed=n, eps=eps)
+    rng = np.random.default_rng(n)
+    acts = [np.arange(n, dtype=np.int32),
+            np.sort(rng.choice(n, size=n - 37, replace=False)).astype(np.int32)]
+    got = {}
+    for sk in (True, False):
+        sim = nb.Simulation(m, x, v, eps=eps, precision=precision, keep_state=True, streamk=sk)
+        st = {"m": m, "x": x, "v": v, "a": a, "j": np.zeros((n, 3)), "s": np.zeros((n, 3)),
+              "c": np.zeros((n, 3)), "t": np.zeros(n), "dt": np.full(n, 2.0 ** -6),
+              "pot": np.zeros(n)}
+        sim.set_state_numpy(st)
+        sim.predict(0.0, out=False)
+        for k, act in enumerate(acts):
+            at = torch.as_tensor(act, device="cuda")
+            o1 = sim.evaluate(at).cpu().numpy()
+            o2 = sim.evaluate(at).cpu().numpy()
+            np.testing.assert_array_equal(o1, o2)
+            got[(sk, k)] = o1
+            if sk and k == 1:
+                _check_eval(torch.as_tensor(o1), oracle.force(m, x, v, a, eps, active=act),
+                            TOL[precision], f"stream-K {precision} n={n}")
+        sim.close()
+    for k in range(2):
+        e = rel_rows(got[(True, k)][0:3].T, got[(False, k)][0:3].T)
+        assert e.max() <= TOL[precision], e.max()
+
+
 def test_evaluate_single_particle(nb, oracle):
     m = np.array([1.0]); x = np.zeros((1, 3)); v = np.zeros((1, 3))
     sim = _sim_with_state(nb, m, x, v, np.zeros((1, 3)), 1e-2, "fp64")
