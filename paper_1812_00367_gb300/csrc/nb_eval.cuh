@@ -139,7 +139,7 @@ struct Prec<NB_FP64> {
         m = self ? 0.0 : m;
         c.p = fma(m, rsqrt_f64(r2), c.p);
     }
-    static __device__ __forceinline__ void finish(const Acc &c, const double *, double o[10]) {
+    static __device__ __forceinline__ void finish(const Acc &c, const double *, int, double o[10]) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             o[k] = c.a[k];
@@ -303,7 +303,7 @@ struct Prec<NB_EX> {
         }
     }
     static __device__ __forceinline__ double to_d(ff a) { return (double)a.hi + (double)a.lo; }
-    static __device__ __forceinline__ void finish(const Acc &c, const double *, double o[10]) {
+    static __device__ __forceinline__ void finish(const Acc &c, const double *, int, double o[10]) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             o[k] = to_d(c.a[k]);
@@ -417,31 +417,47 @@ struct Prec<NB_FP32> {
         c.p = 0.f;
     }
     // Promote the FP32 chunk sums into the FP64 totals and restart them.
-    static __device__ __forceinline__ void flush(Acc &c, double *t64) {
+    // t64: the ten FP64 totals, element q at t64[q * st]
+    static __device__ __forceinline__ void flush(Acc &c, double *t64, int st) {
         tile_done(c);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            t64[k] += (double)c.ca[k];
-            t64[3 + k] += (double)c.cj[k];
-            t64[6 + k] += (double)c.cs[k];
+            t64[k * st] += (double)c.ca[k];
+            t64[(3 + k) * st] += (double)c.cj[k];
+            t64[(6 + k) * st] += (double)c.cs[k];
         }
-        t64[9] += (double)c.cp;
+        t64[9 * st] += (double)c.cp;
         zero(c);
     }
-    static __device__ __forceinline__ void finish(Acc &c, double *t64, double o[10]) {
-        flush(c, t64);
+    static __device__ __forceinline__ void finish(Acc &c, double *t64, int st, double o[10]) {
+        flush(c, t64, st);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) o[k] = t64[k];
-        o[9] = -t64[9];
+        for (int k = 0; k < 9; ++k) o[k] = t64[k * st];
+        o[9] = -t64[9 * st];
     }
 };
 
 // ================================================================ kernel
+// Per-arithmetic launch configuration of the evaluation kernel.
+template <int P>
+struct EvalCfg {
+    static constexpr int stages = kStages;
+    static constexpr int min_blocks = NB_EVAL_MIN_BLOCKS;
+    static constexpr bool t64_smem = false;
+};
+template <>
+struct EvalCfg<NB_FP32> {
+    static constexpr int stages = NB_FP32_STAGES;
+    static constexpr int min_blocks = NB_FP32_MIN_BLOCKS;
+    static constexpr bool t64_smem = NB_FP32_T64_SMEM != 0;
+};
+
 template <int P>
 struct SmemLayout {
-    typename Prec<P>::J tile[kStages][kTJ];
+    typename Prec<P>::J tile[EvalCfg<P>::stages][kTJ];
     double red[10 * kTPB];  // cross-split reduction: group sums, then totals
-    uint64_t bar[kStages];
+    double t64[EvalCfg<P>::t64_smem ? 10 * kTPB : 1];  // FP32 totals, [q][thread]
+    uint64_t bar[EvalCfg<P>::stages];
     int flag;
     long long next_item;
     int fail;
@@ -501,15 +517,16 @@ __device__ __forceinline__ int64_t sk_units(const Dev &d, const EvalLaunch &L) {
 }
 
 template <int P, int MODE>
-__global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, const EvalLaunch L) {
+__global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev d, const EvalLaunch L) {
     using T = Prec<P>;
+    constexpr int kSt = EvalCfg<P>::stages;
     using J = typename T::J;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemLayout<P> &S = *reinterpret_cast<SmemLayout<P> *>(smem_raw);
     const int tid = threadIdx.x;
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&S.bar[s], 1);
+        for (int s = 0; s < kSt; ++s) mbar_init(&S.bar[s], 1);
         S.fail = 0;
         fence_mbar_init();
     }
@@ -595,15 +612,17 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
         if constexpr (P == NB_FP64) T::prepare(me, d);
         typename T::Acc acc;
         T::zero(acc);
-        double t64[10];
+        double t64r[EvalCfg<P>::t64_smem ? 1 : 10];
+        double *t64 = EvalCfg<P>::t64_smem ? S.t64 + tid : t64r;
+        constexpr int t64st = EvalCfg<P>::t64_smem ? kTPB : 1;
 #pragma unroll
-        for (int q = 0; q < 10; ++q) t64[q] = 0.0;
+        for (int q = 0; q < 10; ++q) t64[q * t64st] = 0.0;
 
         const bool warp_active = __any_sync(0xffffffffu, valid);
 
         // prologue: fill the ring
         if (tid == 0) {
-            for (int s = 0; s < kStages && tb + s < te; ++s) {
+            for (int s = 0; s < kSt && tb + s < te; ++s) {
                 mbar_expect_tx(&S.bar[s], kTJ * sizeof(J));
                 tma_load_1d(&S.tile[s][0], jc + (tb + s) * kTJ, kTJ * sizeof(J), &S.bar[s]);
                 pending |= 1u << s;
@@ -611,7 +630,7 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
         }
         bool ok = true;
         for (int64_t tt = tb; tt < te; ++tt) {
-            const int s = (int)((tt - tb) % kStages);
+            const int s = (int)((tt - tb) % kSt);
             if (ok) ok = mbar_wait_bounded(&S.bar[s], (phase >> s) & 1u);
             phase ^= 1u << s;
             if (ok && warp_active) {
@@ -638,7 +657,7 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
                         T::interact(me, tl[k], jbase + k == ji, eps2, eps2f, acc);
                 }
                 if constexpr (P == NB_FP32) {
-                    if ((tt - tb + 1) % kFp32FlushTiles == 0) T::flush(acc, t64);
+                    if ((tt - tb + 1) % kFp32FlushTiles == 0) T::flush(acc, t64, t64st);
                     else T::tile_done(acc);
                 } else if constexpr (P == NB_EX && NB_EX_LAZY && MODE != kModePot) {
                     T::tile_done(acc);
@@ -649,9 +668,9 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
             if (S.fail) break;
             if (tid == 0) {
                 pending &= ~(1u << s);
-                if (tt + kStages < te) {
+                if (tt + kSt < te) {
                     mbar_expect_tx(&S.bar[s], kTJ * sizeof(J));
-                    tma_load_1d(&S.tile[s][0], jc + (tt + kStages) * kTJ, kTJ * sizeof(J), &S.bar[s]);
+                    tma_load_1d(&S.tile[s][0], jc + (tt + kSt) * kTJ, kTJ * sizeof(J), &S.bar[s]);
                     pending |= 1u << s;
                 }
             }
@@ -661,14 +680,14 @@ __global__ void __launch_bounds__(kTPB, NB_EVAL_MIN_BLOCKS) k_eval(const Dev d, 
             // CTA still has in flight, and leave the kernel
             if (tid == 0) {
                 atomicOr(d.err, kErrTimeout);
-                for (int s = 0; s < kStages; ++s)
+                for (int s = 0; s < kSt; ++s)
                     if (pending & (1u << s)) (void)mbar_wait_bounded(&S.bar[s], (phase >> s) & 1u);
             }
             return;
         }
 
         double o[10];
-        T::finish(acc, t64, o);
+        T::finish(acc, t64, t64st, o);
         // lanes sharing an i: butterfly sum (fixed order)
         for (int w = gl >> 1; w >= 1; w >>= 1) {
 #pragma unroll

@@ -41,6 +41,17 @@ constexpr int kTJ = 64;        // j-particles per shared-memory tile
 // measured 5.9 % faster for the whole pair evaluation.
 #define NB_FP64_ALL_FMA 1
 #endif
+// FP32 evaluation: its own ring depth, residency and place of the FP64
+// chunk totals (registers, or shared memory when NB_FP32_T64_SMEM)
+#ifndef NB_FP32_STAGES
+#define NB_FP32_STAGES NB_EVAL_STAGES
+#endif
+#ifndef NB_FP32_MIN_BLOCKS
+#define NB_FP32_MIN_BLOCKS NB_EVAL_MIN_BLOCKS
+#endif
+#ifndef NB_FP32_T64_SMEM
+#define NB_FP32_T64_SMEM 0
+#endif
 constexpr int kStages = NB_EVAL_STAGES;  // TMA pipeline depth
 constexpr int kEvalUnroll = NB_EVAL_UNROLL;
 constexpr int kChunk = 2048;   // particles per select / predict chunk
