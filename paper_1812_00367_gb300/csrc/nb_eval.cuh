@@ -452,14 +452,22 @@ struct EvalCfg<NB_FP32> {
     static constexpr bool t64_smem = NB_FP32_T64_SMEM != 0;
 };
 
+// One piece of work, described by thread 0 for the whole CTA.
+struct PieceRec {
+    long long item, item_end;  // current item / unit and the end of this CTA's work
+    long long tb, te;          // j-tiles of the piece
+    long long local, tile0, pslot0, off, nc, ntj;
+    int c, gl, split, A, tile, sk;  // c < 0: no more work
+};
+
 template <int P>
 struct SmemLayout {
     typename Prec<P>::J tile[EvalCfg<P>::stages][kTJ];
     double red[10 * kTPB];  // cross-split reduction: group sums, then totals
     double t64[EvalCfg<P>::t64_smem ? 10 * kTPB : 1];  // FP32 totals, [q][thread]
     uint64_t bar[EvalCfg<P>::stages];
+    PieceRec pc;
     int flag;
-    long long next_item;
     int fail;
 };
 
@@ -497,18 +505,6 @@ __device__ __forceinline__ void finalize_one(const Dev &d, const EvalLaunch &L, 
     }
 }
 
-// Next work item of this CTA (see the item loop of k_eval).  Ends with a
-// barrier, so the shared slot can be reused.
-template <int P>
-__device__ __forceinline__ int64_t next_item_of(const EvalLaunch &L, const Dev &d, SmemLayout<P> &S,
-                                                int64_t item) {
-    if (L.direct) return item + gridDim.x;
-    __syncthreads();
-    if (threadIdx.x == 0) S.next_item = (long long)atomicAdd(d.item_ctr, 1ull);
-    __syncthreads();
-    return S.next_item;
-}
-
 // Units of a stream-K launch (one cluster): i-tiles x j-tiles.
 __device__ __forceinline__ int64_t sk_units(const Dev &d, const EvalLaunch &L) {
     const int c = L.direct ? L.cluster : 0;
@@ -523,24 +519,8 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
     using J = typename T::J;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemLayout<P> &S = *reinterpret_cast<SmemLayout<P> *>(smem_raw);
+    PieceRec &R = S.pc;
     const int tid = threadIdx.x;
-
-    if (tid == 0) {
-        for (int s = 0; s < kSt; ++s) mbar_init(&S.bar[s], 1);
-        S.fail = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    const int64_t n_items = L.direct ? (int64_t)L.tiles * L.split : *d.n_items;
-    const J *jall = reinterpret_cast<const J *>(d.jarr);
-    const double eps2 = d.eps2;
-    const float eps2f = (float)d.eps2;
-    ff eps2ff;
-    eps2ff.hi = (float)d.eps2;
-    eps2ff.lo = (float)(d.eps2 - (double)eps2ff.hi);
-    uint32_t phase = 0;   // bit s: parity of stage s
-    uint32_t pending = 0; // bit s: a copy into stage s is in flight
 
     // Work: a stream-K launch (one cluster) gives CTA k the unit range
     // [U k / G, U (k+1) / G) and walks it piece by piece (one piece per i-tile
@@ -548,66 +528,90 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
     // direct launches (equal-cost items of one cluster) take a static round
     // robin; planned launches fetch items dynamically, since clusters of a
     // batch give items of unequal cost.  Either way a piece's arithmetic and
-    // the reduction order do not depend on the CTA that runs it.
-    const bool sk = L.direct ? L.streamk != 0 : (d.n_clusters == 1 && d.plan[0].streamk != 0);
-    // stream-K: `item` walks this CTA's unit range and `item_end` closes it
-    int64_t item = blockIdx.x, item_end = n_items;
-    if (sk) {
-        item = sk_begin(sk_units(d, L), gridDim.x, blockIdx.x);
-        item_end = sk_begin(sk_units(d, L), gridDim.x, blockIdx.x + 1);
-    } else if (!L.direct) {
-        if (tid == 0) S.next_item = (long long)atomicAdd(d.item_ctr, 1ull);
-        __syncthreads();
-        item = S.next_item;
+    // the reduction order do not depend on the CTA that runs it.  Thread 0
+    // keeps the piece's bookkeeping in shared memory, so that the pair loop
+    // holds only what it uses in registers.
+    if (tid == 0) {
+        for (int s = 0; s < kSt; ++s) mbar_init(&S.bar[s], 1);
+        S.fail = 0;
+        fence_mbar_init();
+        R.sk = L.direct ? L.streamk != 0 : (d.n_clusters == 1 && d.plan[0].streamk != 0);
+        if (R.sk) {
+            R.item = sk_begin(sk_units(d, L), gridDim.x, blockIdx.x);
+            R.item_end = sk_begin(sk_units(d, L), gridDim.x, blockIdx.x + 1);
+        } else {
+            R.item_end = L.direct ? (int64_t)L.tiles * L.split : *d.n_items;
+            R.item = L.direct ? (int64_t)blockIdx.x : (long long)atomicAdd(d.item_ctr, 1ull);
+        }
     }
-    for (; item < item_end;) {
-        int c, gl, split, A;
-        int64_t item0, tile0, pslot0;
-        if (L.direct) {
-            c = L.cluster; gl = L.gl; split = L.split; A = L.n_active; item0 = 0; tile0 = 0;
-            pslot0 = 0;
-        } else {
-            c = sk ? 0 : find_cluster(d.plan, d.n_clusters, item);
-            const ClusterPlan pl = d.plan[c];
-            gl = pl.gl; split = pl.split; A = pl.active; item0 = pl.item0; tile0 = pl.tile0;
-            pslot0 = pl.pslot0;
-        }
-        const int64_t nc = d.offsets[c + 1] - d.offsets[c];
-        const int64_t ntj = cdiv(nc, kTJ);
-        int64_t local, tb, te;
-        int tile;
-        if (sk) {
-            local = 0;
-            tile = (int)(item / ntj);
-            tb = item - (int64_t)tile * ntj;
-            te = min(ntj, tb + (item_end - item));
-        } else {
-            local = item - item0;
-            tile = (int)(local / split);
-            const int sidx = (int)(local % split);
-            tb = ntj * sidx / split;
-            te = ntj * (sidx + 1) / split;
-        }
-        const int Ti = kTPB / gl;
-        const int ilane = tid / gl;
-        const int jsub = tid % gl;
-        const int iloc = tile * Ti + ilane;
-        const bool valid = iloc < A;
-        const int64_t off = d.offsets[c];
-        const J *jc = jall + d.jofs[c];
-        int64_t gi = off;
-        bool bad_index = false;
-        if (valid) {
-            if (L.identity) gi = off + iloc;
-            else if (L.direct) gi = L.active[iloc];
-            else gi = d.active[off + iloc];
-            if (gi < off || gi >= off + nc) {  // caller-given index outside the cluster
-                atomicOr(d.err, kErrIndex);
-                gi = off;
-                bad_index = true;
+    uint32_t phase = 0;   // bit s: parity of stage s
+    uint32_t pending = 0; // bit s: a copy into stage s is in flight
+
+    for (;;) {
+        // thread 0: describe the current piece (or the end of the work)
+        if (tid == 0) {
+            const int64_t item = R.item;
+            if (item >= R.item_end) {
+                R.c = -1;
+            } else {
+                int c, gl, split, A;
+                int64_t item0, tile0, pslot0;
+                if (L.direct) {
+                    c = L.cluster; gl = L.gl; split = L.split; A = L.n_active; item0 = 0; tile0 = 0;
+                    pslot0 = 0;
+                } else {
+                    c = R.sk ? 0 : find_cluster(d.plan, d.n_clusters, item);
+                    const ClusterPlan pl = d.plan[c];
+                    gl = pl.gl; split = pl.split; A = pl.active; item0 = pl.item0; tile0 = pl.tile0;
+                    pslot0 = pl.pslot0;
+                }
+                const int64_t off = d.offsets[c];
+                const int64_t nc = d.offsets[c + 1] - off;
+                const int64_t ntj = cdiv(nc, kTJ);
+                int tile;
+                int64_t tb, te, local = 0;
+                if (R.sk) {
+                    tile = (int)(item / ntj);
+                    tb = item - (int64_t)tile * ntj;
+                    te = min(ntj, tb + (int64_t)(R.item_end - item));
+                } else {
+                    local = item - item0;
+                    tile = (int)(local / split);
+                    const int sidx = (int)(local % split);
+                    tb = ntj * sidx / split;
+                    te = ntj * (sidx + 1) / split;
+                }
+                R.c = c; R.gl = gl; R.split = split; R.A = A; R.tile = tile;
+                R.tile0 = tile0; R.pslot0 = pslot0; R.local = local;
+                R.off = off; R.nc = nc; R.ntj = ntj; R.tb = tb; R.te = te;
             }
         }
-        const int64_t ji = gi - off;
+        __syncthreads();
+        if (R.c < 0) break;
+
+        const int c = R.c;
+        const int gl = R.gl;
+        const int64_t tb = R.tb, te = R.te;
+        const int ilane = tid / gl;
+        const int jsub = tid % gl;
+        const bool valid = R.tile * (kTPB / gl) + ilane < R.A;
+        const J *jc = reinterpret_cast<const J *>(d.jarr) + d.jofs[c];
+        // this thread's i: global index, bounds-checked against its cluster
+        auto i_of = [&](int il, bool &bad) -> int64_t {
+            const int64_t off = R.off;
+            int64_t g;
+            if (L.identity) g = off + il;
+            else if (L.direct) g = L.active[il];
+            else g = d.active[off + il];
+            bad = g < off || g >= off + R.nc;
+            return bad ? off : g;
+        };
+        int64_t ji = 0;
+        if (valid) {
+            bool bad;
+            ji = i_of(R.tile * (kTPB / gl) + ilane, bad) - R.off;
+            if (bad) atomicOr(d.err, kErrIndex);  // caller-given index outside the cluster
+        }
         typename T::I me = T::load_i(jc, ji);
         if constexpr (P == NB_FP64) T::prepare(me, d);
         typename T::Acc acc;
@@ -617,6 +621,11 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
         constexpr int t64st = EvalCfg<P>::t64_smem ? kTPB : 1;
 #pragma unroll
         for (int q = 0; q < 10; ++q) t64[q * t64st] = 0.0;
+        const double eps2 = d.eps2;
+        const float eps2f = (float)eps2;
+        ff eps2ff;
+        eps2ff.hi = (float)eps2;
+        eps2ff.lo = (float)(eps2 - (double)eps2ff.hi);
 
         const bool warp_active = __any_sync(0xffffffffu, valid);
 
@@ -694,6 +703,11 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
             for (int q = 0; q < 10; ++q) o[q] += __shfl_xor_sync(0xffffffffu, o[q], w);
         }
 
+        // ---- epilogue: the piece's bookkeeping comes back from shared memory
+        const int tile = R.tile, A = R.A, split = R.split;
+        const int Ti = kTPB / gl;
+        const int64_t ntj = R.ntj;
+        const bool sk = R.sk;
         // pieces of this i-tile: split items, or the CTAs whose ranges meet it
         int npieces = split;
         int64_t sk_first = 0, sk_maxp = 0, sk_loc0 = 0;
@@ -706,6 +720,7 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
             // others start inside this one (their local tile index is 0)
             sk_loc0 = tile - sk_begin(U, gridDim.x, sk_first) / ntj;
         }
+        const int64_t pslot0 = R.pslot0;
         // partial-sum slot (doubles) of piece s of this tile: CTA k keeps one
         // slot per i-tile its range touches
         auto piece_slot = [&](int64_t s) -> int64_t {
@@ -713,74 +728,76 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
             return pslot0 + ((int64_t)tile * split + s) * (10 * Ti);
         };
         if (npieces == 1) {
-            if (valid && jsub == 0 && !bad_index) finalize_one<P, MODE>(d, L, c, gi, iloc, o);
-            if (sk) {
-                item += te - tb;
-                __syncthreads();
-            } else {
-                item = next_item_of<P>(L, d, S, item);
+            if (valid && jsub == 0) {
+                bool bad;
+                const int il = tile * Ti + ilane;
+                const int64_t gi = i_of(il, bad);
+                if (!bad) finalize_one<P, MODE>(d, L, c, gi, il, o);
             }
-            continue;
-        }
-        // this CTA's piece of the tile
-        double *part = d.partial + (sk ? piece_slot((int64_t)blockIdx.x - sk_first)
-                                       : pslot0 + local * (int64_t)(10 * Ti));
-        if (jsub == 0) {
+        } else {
+            // this CTA's piece of the tile
+            double *part = d.partial + (sk ? piece_slot((int64_t)blockIdx.x - sk_first)
+                                           : pslot0 + R.local * (int64_t)(10 * Ti));
+            if (jsub == 0) {
 #pragma unroll
-            for (int q = 0; q < 10; ++q) part[q * Ti + ilane] = o[q];
-        }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const int prev = atomicAdd(&d.tile_cnt[tile0 + tile], 1);
-            S.flag = (prev == npieces - 1);
-        }
-        __syncthreads();
-        if (S.flag) {
-            // Last CTA of this i-tile: add the partials of its pieces for every
-            // (i, q) pair in two fixed-order levels.  Level 1: thread (p, r)
-            // sums the r-th contiguous group of pieces of pair p in piece order;
-            // level 2 adds the R group sums in group order.  The order depends
-            // only on (pieces, valid i count), so results are reproducible.
+                for (int q = 0; q < 10; ++q) part[q * Ti + ilane] = o[q];
+            }
             __threadfence();
-            const int nv = min(Ti, A - tile * Ti);     // valid i in this tile
-            const int npair = nv * 10;
-            const int R = max(1, kTPB / npair);
-            for (int w = tid; w < npair * R; w += kTPB) {
-                const int p = w % npair, r = w / npair;
-                const int q = p / nv, il = p % nv;
-                const int s0 = (int)((int64_t)npieces * r / R), s1 = (int)((int64_t)npieces * (r + 1) / R);
-                double acc = 0.0;
-                if (sk) {
-                    for (int sp = s0; sp < s1; ++sp) acc += __ldcg(d.partial + piece_slot(sp) + q * Ti + il);
-                } else {
-                    const double *base = d.partial + piece_slot(0);
-#pragma unroll 4
-                    for (int sp = s0; sp < s1; ++sp) acc += __ldcg(base + (int64_t)sp * (10 * Ti) + q * Ti + il);
-                }
-                S.red[r * npair + p] = acc;
+            __syncthreads();
+            if (tid == 0) {
+                const int prev = atomicAdd(&d.tile_cnt[R.tile0 + tile], 1);
+                S.flag = (prev == npieces - 1);
             }
             __syncthreads();
-            if (tid < nv) {
-                double sum[10];
-#pragma unroll
-                for (int q = 0; q < 10; ++q) {
-                    double acc = 0.0;
-                    for (int r = 0; r < R; ++r) acc += S.red[r * npair + q * nv + tid];
-                    sum[q] = acc;
+            if (S.flag) {
+                // Last CTA of this i-tile: add the partials of its pieces for
+                // every (i, q) pair in two fixed-order levels.  Level 1: thread
+                // (p, r) sums the r-th contiguous group of pieces of pair p in
+                // piece order; level 2 adds the R group sums in group order.  The
+                // order depends only on (pieces, valid i count), so results are
+                // reproducible.
+                __threadfence();
+                const int nv = min(Ti, A - tile * Ti);     // valid i in this tile
+                const int npair = nv * 10;
+                const int Rg = max(1, kTPB / npair);
+                for (int w = tid; w < npair * Rg; w += kTPB) {
+                    const int p = w % npair, r = w / npair;
+                    const int q = p / nv, il = p % nv;
+                    const int s0 = (int)((int64_t)npieces * r / Rg), s1 = (int)((int64_t)npieces * (r + 1) / Rg);
+                    double acc2 = 0.0;
+                    if (sk) {
+                        for (int sp = s0; sp < s1; ++sp) acc2 += __ldcg(d.partial + piece_slot(sp) + q * Ti + il);
+                    } else {
+                        const double *base = d.partial + piece_slot(0);
+#pragma unroll 4
+                        for (int sp = s0; sp < s1; ++sp) acc2 += __ldcg(base + (int64_t)sp * (10 * Ti) + q * Ti + il);
+                    }
+                    S.red[r * npair + p] = acc2;
                 }
-                const int il = tile * Ti + tid;
-                int64_t g2;
-                if (L.identity) g2 = off + il;
-                else if (L.direct) g2 = L.active[il];
-                else g2 = d.active[off + il];
-                if (g2 >= off && g2 < off + nc) finalize_one<P, MODE>(d, L, c, g2, il, sum);
+                __syncthreads();
+                if (tid < nv) {
+                    double sum[10];
+#pragma unroll
+                    for (int q = 0; q < 10; ++q) {
+                        double a2 = 0.0;
+                        for (int r = 0; r < Rg; ++r) a2 += S.red[r * npair + q * nv + tid];
+                        sum[q] = a2;
+                    }
+                    const int il = tile * Ti + tid;
+                    bool bad;
+                    const int64_t g2 = i_of(il, bad);
+                    if (!bad) finalize_one<P, MODE>(d, L, c, g2, il, sum);
+                }
+                if (tid == 0) d.tile_cnt[R.tile0 + tile] = 0;
             }
-            if (tid == 0) d.tile_cnt[tile0 + tile] = 0;
         }
+        // next piece: every thread is done with this piece's record
         __syncthreads();
-        if (sk) item += te - tb;
-        else item = next_item_of<P>(L, d, S, item);
+        if (tid == 0) {
+            if (R.sk) R.item += R.te - R.tb;
+            else if (L.direct) R.item += gridDim.x;
+            else R.item = (long long)atomicAdd(d.item_ctr, 1ull);
+        }
     }
 }
 

@@ -50,7 +50,7 @@ constexpr int kTJ = 64;        // j-particles per shared-memory tile
 #define NB_FP32_MIN_BLOCKS NB_EVAL_MIN_BLOCKS
 #endif
 #ifndef NB_FP32_T64_SMEM
-#define NB_FP32_T64_SMEM 0
+#define NB_FP32_T64_SMEM 1
 #endif
 constexpr int kStages = NB_EVAL_STAGES;  // TMA pipeline depth
 constexpr int kEvalUnroll = NB_EVAL_UNROLL;
