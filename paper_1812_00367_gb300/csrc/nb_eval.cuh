@@ -446,6 +446,12 @@ struct EvalCfg {
     static constexpr bool t64_smem = false;
 };
 template <>
+struct EvalCfg<NB_EX> {
+    static constexpr int stages = kStages;
+    static constexpr int min_blocks = NB_EX_MIN_BLOCKS;
+    static constexpr bool t64_smem = false;
+};
+template <>
 struct EvalCfg<NB_FP32> {
     static constexpr int stages = NB_FP32_STAGES;
     static constexpr int min_blocks = NB_FP32_MIN_BLOCKS;

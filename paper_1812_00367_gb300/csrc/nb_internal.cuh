@@ -49,6 +49,9 @@ constexpr int kTJ = 64;        // j-particles per shared-memory tile
 #ifndef NB_FP32_MIN_BLOCKS
 #define NB_FP32_MIN_BLOCKS NB_EVAL_MIN_BLOCKS
 #endif
+#ifndef NB_EX_MIN_BLOCKS
+#define NB_EX_MIN_BLOCKS NB_EVAL_MIN_BLOCKS
+#endif
 #ifndef NB_FP32_T64_SMEM
 #define NB_FP32_T64_SMEM 1
 #endif
