@@ -30,6 +30,11 @@
  * interpolation on polynomials, a 6x6 Hermite solve, the Kepler problem in
  * closed form with measured convergence order ~6, the criterion on
  * exponential derivative ladders, scheduler brute force, energy conservation.
+ * The 4th-order variant (Makino & Aarseth 1992; tests/test_oracle_hermite4.py):
+ * exactness of its predictor / corrector / cubic interpolation on
+ * polynomials, Aarseth's criterion on exponential ladders and under time
+ * rescaling, Kepler convergence order ~4, energy and momentum.  Every function
+ * here has a pin; none is "parity unpinned".
  */
 #include <math.h>
 #include <stdint.h>

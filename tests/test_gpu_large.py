@@ -5,6 +5,8 @@
 * N = 2^20 Plummer with a Kroupa-like mass spectrum, eps = 1e-5: 4096 active
   particles evaluated on the GPU, 512 of them checked against the oracle, in
   FP64, EX and FP32 (max and 99.9th percentile relative errors printed).
+* N = 4,194,304 (two Hernquist spheres), the largest workload: 1024 active,
+  256 checked, FP64 and EX.
 """
 import numpy as np
 import pytest
@@ -92,3 +94,32 @@ def test_n1m_kroupa_subsample(nb, oracle, kroupa1m, precision):
     for k, v in e.items():
         assert v.max() <= TOL[precision], (k, v.max())
     sim.close()
+
+
+@pytest.fixture(scope="module")
+def merger4m():
+    return ic.hernquist_merger(1 << 21, seed=5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "ex"])
+def test_n4m_merger_subsample(nb, oracle, merger4m, precision):
+    """The largest system of the workloads: two Hernquist spheres of 2^21
+    particles on a parabolic orbit (N = 4,194,304, eps = 1e-3).  1024 active
+    particles spread over both spheres (stream-K ranges over 65536 j-tiles);
+    256 of them checked against the oracle one by one."""
+    m, x, v = merger4m
+    n, eps = len(m), 1e-3
+    sim = nb.Simulation(m, x, v, eps=eps, precision=precision, keep_state=True)
+    a = np.zeros((n, 3))
+    sim.set_state_numpy({"m": m, "x": x, "v": v, "a": a, "j": a, "s": a, "c": a,
+                         "t": np.zeros(n), "dt": np.full(n, 2.0 ** -6), "pot": np.zeros(n)})
+    sim.predict(0.0, out=False)
+    act = np.linspace(0, n - 1, 1024).astype(np.int32)
+    out = sim.evaluate(torch.as_tensor(act, device="cuda")).cpu().numpy()
+    sim.sync()
+    sim.close()
+    pick = np.arange(0, 1024, 4)
+    ref = oracle.force(m, x, v, a, eps, active=act[pick])
+    e = _errors(out[:, pick], ref)
+    for k, err in e.items():
+        assert err.max() <= TOL[precision], (k, err.max())
