@@ -49,8 +49,8 @@ WORKLOAD = (f"Plummer N={N}, equal masses, Henon units, eps={EPS:g}, block steps
 # launch of one ncu capture of this workload (summary and command in
 # profiles/).  It holds for the kernel sources it was taken on (SHA-256 of
 # EVAL_SOURCES below); after any change to them it is reported as null.
-EVAL_TRAFFIC = {"bytes_per_launch": 6480502, "launches": 1520,
-                "sources_sha256": "c8345926a9dac63f35c7fcfd2e09957a27f7fa7d367a4f68007184798d3cff4d"}
+EVAL_TRAFFIC = {"bytes_per_launch": 5927985, "launches": 1520,
+                "sources_sha256": "aeee88df27e8b9f8dc6845ae731a1bb081d862b71a3a5907c8065523ed215be7"}
 EVAL_SOURCES = ("nb_eval.cuh", "nb_eval_fp64.cu", "nb_step.cuh", "nb_internal.cuh")
 
 
