@@ -173,21 +173,6 @@ struct Prec<NB_EX> {
         for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = ff{0.f, 0.f};
         c.p = ff{0.f, 0.f};
     }
-    // 1/sqrt(r2) in float-float: SFU seed y0, residual e = 1 - r2 y0^2 from the
-    // exact square of y0 and FMA-exact products, then y0 (1 + e/2 + 3e^2/8).
-    static __device__ __forceinline__ ff rsqrt_ff(ff r2) {
-        float y0;
-        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.hi));
-        const float p = __fmul_rn(y0, y0);
-        const float pe = __fmaf_rn(y0, y0, -p);
-        const float u = __fmul_rn(r2.hi, p);
-        float ue = __fmaf_rn(r2.hi, p, -u);
-        ue = __fmaf_rn(r2.hi, pe, ue);
-        ue = __fmaf_rn(r2.lo, p, ue);
-        const float e = __fsub_rn(__fsub_rn(1.0f, u), ue);
-        const float corr = __fmul_rn(__fmul_rn(y0, e), __fmaf_rn(e, 0.375f, 0.5f));
-        return ff_renorm(y0, corr);
-    }
     static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self, double,
                                                     float, Acc &c, ff eps2) {
         const float4 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3], q4 = jj.q[4];
@@ -201,20 +186,20 @@ struct Prec<NB_EX> {
         a[0] = ff_sub(ff{q2.w, q3.w}, i.a[0]);
         a[1] = ff_sub(ff{q4.x, q4.z}, i.a[1]);
         a[2] = ff_sub(ff{q4.y, q4.w}, i.a[2]);
-        ff r2 = NB_EX_LAZY ? ff_dot3_add(r, r, eps2) : ff_add(ff_dot3(r, r), eps2);
+        ff r2 = NB_EX_LAZY ? ff_dot3_add_lazy(r, r, eps2) : ff_add(ff_dot3(r, r), eps2);
         ff m = ff{q0.w, q1.w};
         if (self) {
             r2 = ff{1.f, 0.f};
             m = ff{0.f, 0.f};
         }
         const ff y = rsqrt_ff(r2);
-        const ff rv = ff_dot3(r, v);
+        const ff rv = NB_EX_LAZY ? ff_dot3_lazy(r, v) : ff_dot3(r, v);
         ff y2, my, q, w, al, ze, al3, be3;
         if constexpr (NB_EX_LAZY) {
             y2 = ff_sqr_lazy(y);
             my = ff_mul_lazy(m, y);
             q = ff_mul_lazy(my, y2);
-            w = ff_dot3x2_add(v, v, r, a, ff{0.f, 0.f});
+            w = ff_dot3x2_lazy(v, v, r, a);
             al = ff_mul_lazy(rv, y2);
             ze = ff_mul_lazy(w, y2);
             al3 = ff_mul_f_lazy(al, 3.0f);

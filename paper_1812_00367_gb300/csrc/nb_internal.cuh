@@ -456,6 +456,87 @@ __device__ __forceinline__ ff ff_fnma_lazy(ff b, ff c, ff a) {
     two_sum(a.hi, -p, s, e);
     return ff{s, __fadd_rn(e, __fsub_rn(a.lo, pe))};
 }
+// 1/sqrt(r2) in float-float: SFU seed y0, residual e = 1 - r2 y0^2 from the
+// exact square of y0 and FMA-exact products, then y0 (1 + e/2 + 3e^2/8).
+// Lazy form: y0 + corr as it is (|corr| ~ 2^-22 |y0|).  Domain: the normal
+// FP32 range of r2.hi.
+__device__ __forceinline__ ff rsqrt_ff(ff r2) {
+    float y0;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.hi));
+    const float p = __fmul_rn(y0, y0);
+    const float pe = __fmaf_rn(y0, y0, -p);
+    const float u = __fmul_rn(r2.hi, p);
+    float ue = __fmaf_rn(r2.hi, p, -u);
+    ue = __fmaf_rn(r2.hi, pe, ue);
+    ue = __fmaf_rn(r2.lo, p, ue);
+    const float e = __fsub_rn(__fsub_rn(1.0f, u), ue);
+    const float corr = __fmul_rn(__fmul_rn(y0, e), __fmaf_rn(e, 0.375f, 0.5f));
+    if constexpr (NB_EX_LAZY) return ff{y0, corr};
+    else return ff_renorm(y0, corr);
+}
+
+// a.b, unnormalised (hi + lo with every error term in lo)
+__device__ __forceinline__ ff ff_dot3_lazy(const ff a[3], const ff b[3]) {
+    float p[3], lo;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = __fmul_rn(a[k].hi, b[k].hi);
+    lo = __fmaf_rn(a[0].hi, b[0].hi, -p[0]);
+#pragma unroll
+    for (int k = 1; k < 3; ++k) lo = __fmaf_rn(a[k].hi, b[k].hi, -p[k]) + lo;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo = __fmaf_rn(a[k].hi, b[k].lo, lo);
+        lo = __fmaf_rn(a[k].lo, b[k].hi, lo);
+    }
+    float s = p[0], e;
+#pragma unroll
+    for (int k = 1; k < 3; ++k) {
+        two_sum(s, p[k], s, e);
+        lo = __fadd_rn(lo, e);
+    }
+    return ff{s, lo};
+}
+// a0.b0 + a1.b1, unnormalised
+__device__ __forceinline__ ff ff_dot3x2_lazy(const ff a0[3], const ff b0[3], const ff a1[3],
+                                             const ff b1[3]) {
+    float p[6], lo = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = __fmul_rn(a0[k].hi, b0[k].hi);
+        p[3 + k] = __fmul_rn(a1[k].hi, b1[k].hi);
+        lo = __fmaf_rn(a0[k].hi, b0[k].hi, -p[k]) + lo;
+        lo = __fmaf_rn(a1[k].hi, b1[k].hi, -p[3 + k]) + lo;
+        lo = __fmaf_rn(a0[k].hi, b0[k].lo, lo);
+        lo = __fmaf_rn(a0[k].lo, b0[k].hi, lo);
+        lo = __fmaf_rn(a1[k].hi, b1[k].lo, lo);
+        lo = __fmaf_rn(a1[k].lo, b1[k].hi, lo);
+    }
+    float s = p[0], e;
+#pragma unroll
+    for (int k = 1; k < 6; ++k) {
+        two_sum(s, p[k], s, e);
+        lo = __fadd_rn(lo, e);
+    }
+    return ff{s, lo};
+}
+// a.b + c, unnormalised
+__device__ __forceinline__ ff ff_dot3_add_lazy(const ff a[3], const ff b[3], ff c) {
+    float p[3], lo = c.lo;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = __fmul_rn(a[k].hi, b[k].hi);
+        lo = __fmaf_rn(a[k].hi, b[k].hi, -p[k]) + lo;
+        lo = __fmaf_rn(a[k].hi, b[k].lo, lo);
+        lo = __fmaf_rn(a[k].lo, b[k].hi, lo);
+    }
+    float s = c.hi, e;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        two_sum(s, p[k], s, e);
+        lo = __fadd_rn(lo, e);
+    }
+    return ff{s, lo};
+}
 // a.b + c, one renormalisation
 __device__ __forceinline__ ff ff_dot3_add(const ff a[3], const ff b[3], ff c) {
     float p[3], lo = c.lo;

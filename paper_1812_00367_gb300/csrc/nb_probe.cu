@@ -1,7 +1,10 @@
 // nb_probe.cu -- FMA throughput probes (measurement aid, include/nb_probe.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "../../include/nb_probe.h"
+#include "nb_internal.cuh"
 
 namespace {
 constexpr int kChains = 8;
@@ -162,4 +165,33 @@ extern "C" nb_status nb_selftest_wait_timeout(double budget_seconds, void *strea
     cudaFree(d_err);
     if (e != cudaSuccess) return NB_ECUDA;
     return (h_err & nb::kErrTimeout) ? NB_ETIMEOUT : NB_OK;
+}
+
+// ------------------------------------------------ reciprocal square roots
+namespace {
+__global__ void k_rsqrt(int which, const double *x, double *y, int64_t n, double neg_zero) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[k];
+        if (which == 0) {
+            y[k] = nb::rsqrt_f64_fma(v, neg_zero);
+        } else {
+            nb::ff r2;
+            r2.hi = __double2float_rn(v);
+            r2.lo = __double2float_rn(v - (double)r2.hi);
+            const nb::ff r = nb::rsqrt_ff(r2);
+            y[k] = (double)r.hi + (double)r.lo;
+        }
+    }
+}
+}  // namespace
+
+extern "C" nb_status nb_probe_rsqrt(int32_t which, const double *x, double *y, int64_t n,
+                                    void *stream) {
+    if (which != 0 && which != 1) return NB_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !y))) return NB_EINVAL;
+    if (n == 0) return NB_OK;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    k_rsqrt<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(which, x, y, n, -0.0);
+    return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ECUDA;
 }

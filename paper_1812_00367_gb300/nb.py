@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
             "nb_free": ([vp], None),
             "nb_probe_fma_peak": ([i32, i64, vp, pd, pd], C.c_int),
             "nb_selftest_wait_timeout": ([d, vp], C.c_int),
+            "nb_probe_rsqrt": ([i32, vp, vp, i64, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -329,6 +330,13 @@ class Simulation:
             a = np.asarray(st[f], dtype=np.float64)
             host[f] = np.ascontiguousarray(a.T if f in VECTOR_FIELDS else a)
         nb_set_state(self.ctx, host_state(host))
+
+
+def nb_probe_rsqrt(which: int, x, y, stream=None):
+    """y = 1/sqrt(x) elementwise with the evaluation kernel's own reciprocal
+    square root (which = 0: FP64, 1: float-float); x, y: device float64 tensors."""
+    _check(load().nb_probe_rsqrt(int(which), _ptr(x), _ptr(y), int(x.numel()),
+                                 _stream_handle(stream)))
 
 
 def nb_selftest_wait_timeout(budget_seconds: float, stream=None) -> int:

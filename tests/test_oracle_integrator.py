@@ -282,3 +282,36 @@ def test_jerk_snap_crackle_vs_finite_differences(oracle):
         for got, fd, tol in ((J[k], fd_j, 1e-8), (S[k], fd_s, 1e-5), (Cr[k], fd_c, 1e-3)):
             err = np.linalg.norm(got - fd, axis=1) / np.linalg.norm(fd, axis=1)
             assert err.max() < tol, (tol, err.max())
+
+
+def _kepler_block_energy(oracle, eta, order=6, orbits=10):
+    m = np.array([0.5, 0.5])
+    r0, v0 = _kepler_state(0.0)
+    x = np.stack([-0.5 * r0, 0.5 * r0]); v = np.stack([-0.5 * v0, 0.5 * v0])
+    sim = oracle.Sim(m, x, v, eps=0.0, eta=eta, order=order).init()
+    t_end = math.floor(orbits * 2 * math.pi / 0.125) * 0.125
+    e0 = sum(sim.energy(0.0)[:2])
+    sim.run(t_end)
+    assert np.all(sim.t == t_end)
+    return abs(sum(sim.energy(t_end)[:2]) - e0) / abs(e0), sim.block_steps
+
+
+def test_kepler_block_steps_energy_and_eta_scaling(oracle):
+    """e = 0.5, eps = 0, block steps on the criterion (eta 0.4 then 0.2):
+    energy error below 1e-6 per orbit, and falling by more than 2^5 when eta
+    halves (the step is proportional to eta; 6th order)."""
+    e1, n1 = _kepler_block_energy(oracle, 0.4)
+    e2, n2 = _kepler_block_energy(oracle, 0.2)
+    assert e1 / 10 < 1e-6, e1
+    assert e1 / e2 > 32.0, (e1, e2)
+    assert 1.5 < n2 / n1 < 2.5, (n1, n2)
+
+
+def test_kepler4_block_steps_eta_scaling(oracle):
+    """The 4th-order scheme's Aarseth step is proportional to sqrt(eta): halving
+    eta shortens steps by sqrt(2) and cuts the energy error by about 4."""
+    e1, n1 = _kepler_block_energy(oracle, 0.02, order=4)
+    e2, n2 = _kepler_block_energy(oracle, 0.01, order=4)
+    assert e1 / 10 < 1e-5, e1
+    assert e1 / e2 > 2.5, (e1, e2)
+    assert 1.2 < n2 / n1 < 1.7, (n1, n2)
