@@ -49,6 +49,8 @@ struct nb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;      // caller's stream (launches, graph replays)
     cudaStream_t cap_stream = nullptr;  // private stream used only for capture
+    cudaStream_t cap_side = nullptr;    // second capture branch (predictor)
+    cudaEvent_t fork = nullptr, join = nullptr;
     nb_params p{};
     int64_t n = 0;
     int32_t nc = 1;
@@ -155,8 +157,14 @@ cudaError_t enqueue_step(nb_ctx *ctx, cudaStream_t st, int slot) {
     cudaError_t e;
     if ((e = launch_select_min(ctx->d, st)) != cudaSuccess) return e;
     if ((e = launch_select_compact(ctx->d, 0.0, st)) != cudaSuccess) return e;
+    // the planner and the predictor both need only the selection: two graph
+    // branches, joined before the evaluation
+    if ((e = cudaEventRecord(ctx->fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ctx->cap_side, ctx->fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_predict(ctx->d, 0, 0, 0.0, ctx->cap_side)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ctx->join, ctx->cap_side)) != cudaSuccess) return e;
     if ((e = launch_plan_ex(ctx->d, 0, 1, st)) != cudaSuccess) return e;
-    if ((e = launch_predict(ctx->d, 0, 0, 0.0, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, ctx->join, 0)) != cudaSuccess) return e;
     EvalLaunch L{};
     if (slot >= 0 && (e = cudaEventRecordWithFlags(ctx->ev[2 * slot], st, cudaEventRecordExternal)) != cudaSuccess)
         return e;
@@ -305,6 +313,9 @@ void nb_free(nb_ctx *ctx) {
     if (ctx->h_tend) cudaFreeHost(ctx->h_tend);
     for (cudaEvent_t ev : ctx->ev) cudaEventDestroy(ev);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->cap_side) cudaStreamDestroy(ctx->cap_side);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
     delete ctx;
 }
 
@@ -348,6 +359,9 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_busy, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_tend, sizeof(double));
     if (e != cudaSuccess) {
