@@ -16,15 +16,20 @@
 // on the integer pipe).  The 4th-order scheme (Makino & Aarseth 1992) keeps
 // A0, A1 and the potential only (interact4: 32 FP64 instructions per pair).
 //
-// Work decomposition: a work item is (cluster, i-tile, j-range).  An i-tile
-// holds kTPB / gl active particles; gl lanes of a warp share one i and take
-// every gl-th j of each tile (gl = 1: i-parallel, j broadcast from shared
-// memory; gl = 32: j-parallel for tiny active sets, warp-shuffle reduction).
-// j-tiles of kTJ particles are copied global -> shared by the TMA engine
-// (cp.async.bulk) into a kStages-deep ring guarded by mbarriers.  When the j
-// range of a cluster is split over S items, each item writes FP64 partial
-// sums; the CTA that finishes an i-tile last (atomic counter) adds the S
-// partials in split order (deterministic) and finalises.
+// Work decomposition: a piece of work is (cluster, i-tile, j-range).  An
+// i-tile holds kTPB / gl active particles; gl lanes of a warp share one i and
+// take every gl-th j of each tile (gl = 1: i-parallel, j broadcast from
+// shared memory; gl = 32: j-parallel for tiny active sets, warp-shuffle
+// reduction).  A batch of clusters is cut into split items (each cluster's j
+// range split S ways, items fetched dynamically); a single cluster into
+// stream-K ranges (CTA k takes units [U k / G, U (k+1) / G) of the U =
+// i-tiles x j-tiles units).  j-tiles of kTJ particles are copied global ->
+// shared by the TMA engine (cp.async.bulk) into a ring of stages guarded by
+// mbarriers.  When an i-tile's j range is covered by several pieces, each
+// writes FP64 partial sums; the CTA that finishes the i-tile last (atomic
+// counter) adds them in piece order (deterministic) and finalises.  Thread 0
+// describes each piece in a shared-memory record so that the pair loop keeps
+// only its own state in registers.
 #pragma once
 
 #include "nb_internal.cuh"
