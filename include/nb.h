@@ -275,6 +275,7 @@ nb_status nb_autotune(nb_ctx *ctx, const char *cache_path);
  *   active   : DEVICE int32 [n_active], indices in [0, n); 0 <= n_active <=
  *              32768; duplicates allowed
  *   out      : DEVICE double [10][n_active]: acc[3], jerk[3], snap[3], pot
+ *              (the 6th-order pair terms; a 4th-order caller ignores snap)
  *   stream   : cudaStream_t (NULL = legacy default); the call synchronises it
  *              to read its error word
  * The first call on a device looks up the array's device address with that
