@@ -751,10 +751,22 @@ def cpu_baseline(seconds: float):
         steps += 1
     dt = time.perf_counter() - t1
     value = (sim.interactions - inter0) / dt
-    return {"value": value, "unit": UNIT, "cores": nb_oracle.num_threads(), "kind": "oracle",
+    cores = nb_oracle.num_threads()
+    # one core: the oracle's evaluation of 2048 active particles against all
+    # N on the current state (a block step of one core could last minutes)
+    nb_oracle.set_threads(1)
+    act1 = np.arange(0, N, N // 2048, dtype=np.int64)[:2048]
+    t2 = time.perf_counter()
+    nb_oracle.force(sim.m, sim.x, sim.v, sim.a, EPS, active=act1)
+    dt1 = time.perf_counter() - t2
+    nb_oracle.set_threads(cores)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"oracle start-up of the same N={N} Plummer system ({t_init:.1f} s, untimed), "
                       f"then its first {steps} block steps ({dt:.1f} s timed)",
-            "init_interactions_per_s": inter0 / t_init}
+            "init_interactions_per_s": inter0 / t_init,
+            "single_core": {"value": len(act1) * (N - 1) / dt1, "cores": 1,
+                            "sample": f"evaluation of {len(act1)} active particles against all "
+                                      f"{N} ({dt1:.1f} s) on one thread"}}
 
 
 def reference_arm(args, ws, rank):

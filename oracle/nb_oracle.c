@@ -613,3 +613,14 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the parallel loops from now on (>= 1; ignored without OpenMP).
+ * Results do not depend on it: each i sums its j in a fixed order. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -77,6 +77,8 @@ def lib():
             L.orc_underflows.argtypes = [C.c_void_p]
             L.orc_underflows.restype = C.c_int64
             L.orc_num_threads.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = None
             L.orc_predict4.argtypes = [C.c_int64] + [_D] * 5 + [C.c_double, _D, _D]
             L.orc_correct4.argtypes = [C.c_double] + [_D] * 8
             L.orc_interp4.argtypes = [C.c_double] + [_D] * 6
@@ -101,6 +103,11 @@ def _f64(a, shape=None) -> np.ndarray:
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
 
 
 def force(m, xp, vp, ap, eps, active=None):
