@@ -265,7 +265,7 @@ nb_status nb_autotune(nb_ctx *ctx, const char *cache_path);
  * (cudaMalloc can synchronise the whole device).  nb_init allocates scratch,
  * so those callers cannot use nb_evaluate.
  * This entry needs no context and allocates nothing: its working space (packed j
- * tiles, split partial sums, tile counters; about 5.3 MB) is a fixed array
+ * tiles, split partial sums, tile counters; about 5.8 MB) is a fixed array
  * compiled into the library, which every GPU that loads libnb keeps until the
  * process exits.
  *   jpred    : DEVICE double [10][n]: x[3], v[3], a[3], m of every particle

@@ -12,9 +12,10 @@
 // with the large alpha terms cancelling inside each pair before it is summed
 // (that keeps the FP32 path within its bound on strongly cancelling sums).
 // Every per-pair operation is a multiply, an add or a fused multiply-add:
-// 53 FP64 instructions per pair on the FP64 path (one exact doubling is done
-// on the integer pipe).  The 4th-order scheme (Makino & Aarseth 1992) keeps
-// A0, A1 and the potential only (interact4: 32 FP64 instructions per pair).
+// 52 FP64 instructions per pair on the FP64 path (one exact doubling is done
+// on the integer pipe; the potential m y is summed in float-float on the FP32
+// pipe, NB_FP64_POT_FF).  The 4th-order scheme (Makino & Aarseth 1992) keeps
+// A0, A1 and the potential only (interact4: 31 FP64 instructions per pair).
 //
 // Work decomposition: a piece of work is (cluster, i-tile, j-range).  An
 // i-tile holds kTPB / gl active particles; gl lanes of a warp share one i and
@@ -50,6 +51,9 @@ struct Prec<NB_FP64> {
     };
     struct Acc {
         double a[3], j[3], s[3], p;
+#if NB_FP64_POT_FF
+        ff pf;  // the current j-tile's potential as a float pair
+#endif
     };
     static __device__ __forceinline__ void prepare(I &i, const Dev &d) {
         i.m1 = d.neg_one;
@@ -82,7 +86,36 @@ struct Prec<NB_FP64> {
 #pragma unroll
         for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = 0.0;
         c.p = 0.0;
+#if NB_FP64_POT_FF
+        c.pf = ff{0.f, 0.f};
+#endif
     }
+    // potential term m y: FP64 DFMA, or float-float on the FP32 pipe
+    static __device__ __forceinline__ void pot_term(const J &jj, bool self, double m, double y,
+                                                    Acc &c) {
+#if NB_FP64_POT_FF
+        (void)m;
+        const float2 mf = jj.mf;
+        const ff yf = ff_from_pos_double(y);
+        const ff mff = ff{self ? 0.f : mf.x, self ? 0.f : mf.y};
+        // renormalised every term (|lo| stays below half an ulp of hi): a
+        // 64-term tile sum is good to ~2^-45, and tiles add up in FP64
+        c.pf = ff_add(c.pf, ff_mul_lazy(mff, yf));
+#else
+        (void)jj;
+        (void)self;
+        c.p = fma(m, y, c.p);
+#endif
+    }
+#if NB_FP64_POT_FF
+    // End of a j-tile: the tile's float-pair potential joins the FP64 total.
+    static __device__ __forceinline__ void tile_done(Acc &c) {
+        c.p += (double)c.pf.hi + (double)c.pf.lo;
+        c.pf = ff{0.f, 0.f};
+    }
+#else
+    static __device__ __forceinline__ void tile_done(Acc &) {}
+#endif
     static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self,
                                                     double eps2, float, Acc &c) {
         const double2 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3], q4 = jj.q[4];
@@ -95,7 +128,7 @@ struct Prec<NB_FP64> {
         m = self ? 0.0 : m;
         const double y = NB_FP64_ALL_FMA ? rsqrt_f64_fma(r2, i.nz) : rsqrt_f64(r2);
         const double y2 = mul(i, y, y);
-        c.p = fma(m, y, c.p);                      // potential: sum m y
+        pot_term(jj, self, m, y, c);               // potential: sum m y
         const double q = mul(i, mul(i, m, y2), y); // m y^3
         const double rv = fma(rx, vx, fma(ry, vy, mul(i, rz, vz)));
         const double w = fma(vx, vx, fma(vy, vy, fma(vz, vz, fma(rx, ax, fma(ry, ay, mul(i, rz, az))))));
@@ -113,7 +146,7 @@ struct Prec<NB_FP64> {
         c.s[0] = fma(q, w2x, c.s[0]); c.s[1] = fma(q, w2y, c.s[1]); c.s[2] = fma(q, w2z, c.s[2]);
     }
     // 4th-order pair term (Makino & Aarseth 1992): A0 = q r, A1 = q (v - 3 alpha r);
-    // 32 FP64 instructions
+    // 31 FP64 instructions (32 without NB_FP64_POT_FF)
     static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self,
                                                      double eps2, float, Acc &c) {
         const double2 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
@@ -125,7 +158,7 @@ struct Prec<NB_FP64> {
         m = self ? 0.0 : m;
         const double y = NB_FP64_ALL_FMA ? rsqrt_f64_fma(r2, i.nz) : rsqrt_f64(r2);
         const double y2 = mul(i, y, y);
-        c.p = fma(m, y, c.p);
+        pot_term(jj, self, m, y, c);
         const double q = mul(i, mul(i, m, y2), y);
         const double rv = fma(rx, vx, fma(ry, vy, mul(i, rz, vz)));
         const double al3 = mul(i, 3.0, mul(i, rv, y2));
@@ -151,7 +184,11 @@ struct Prec<NB_FP64> {
             o[3 + k] = c.j[k];
             o[6 + k] = c.s[k];
         }
+#if NB_FP64_POT_FF
+        o[9] = -(c.p + ((double)c.pf.hi + (double)c.pf.lo));
+#else
         o[9] = -c.p;
+#endif
     }
 };
 
@@ -665,6 +702,8 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
                     if ((tt - tb + 1) % kFp32FlushTiles == 0) T::flush(acc, t64, t64st);
                     else T::tile_done(acc);
                 } else if constexpr (P == NB_EX && NB_EX_LAZY && MODE != kModePot) {
+                    T::tile_done(acc);
+                } else if constexpr (P == NB_FP64 && NB_FP64_POT_FF && MODE != kModePot) {
                     T::tile_done(acc);
                 }
             }

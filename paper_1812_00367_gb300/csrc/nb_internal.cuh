@@ -73,10 +73,34 @@ constexpr uint32_t kErrIndex = 4u;   // a caller-given index outside its cluster
 constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
 
 // ------------------------------------------------------------ packed j-data
-// FP64: x, y, z, m, vx, vy, vz, ax, ay, az as five 16-byte pairs.
+#ifndef NB_FP64_POT_FF
+// 1: the FP64 pair terms sum the potential in float-float on the FP32 pipe
+// (m y from the mass's float pair and y's bits; renormalised every term, a
+// j-tile's sum added to an FP64 total), one DFMA fewer per pair: measured
+// +1.5 % FP64 pair rate, potential within 1e-12 of the oracle at N = 2^20
+// (the j record grows from 80 to 96 bytes)
+#define NB_FP64_POT_FF 1
+#endif
+// FP64: x, y, z, m, vx, vy, vz, ax, ay, az as five 16-byte pairs (and, with
+// NB_FP64_POT_FF, the mass as a float pair).
 struct alignas(16) J64 {
     double2 q[5];  // (x,y) (z,m) (vx,vy) (vz,ax) (ay,az)
+#if NB_FP64_POT_FF
+    float2 mf;     // (m_hi, m_lo)
+    float2 pad_;
+#endif
 };
+// Fill the record's float-pair mass (no-op without NB_FP64_POT_FF).
+__host__ __device__ inline void j64_set_mass_split(J64 &w, double m) {
+#if NB_FP64_POT_FF
+    const float hi = (float)m;
+    w.mf = make_float2(hi, (float)(m - (double)hi));
+    w.pad_ = make_float2(0.f, 0.f);
+#else
+    (void)w;
+    (void)m;
+#endif
+}
 // EX: hi/lo single pairs: (xh,yh,zh,mh) (xl,yl,zl,ml) (vxh,vyh,vzh,axh)
 //     (vxl,vyl,vzl,axl) (ayh,azh,ayl,azl)
 struct alignas(16) JEX {
@@ -473,6 +497,18 @@ __device__ __forceinline__ ff rsqrt_ff(ff r2) {
     const float corr = __fmul_rn(__fmul_rn(y0, e), __fmaf_rn(e, 0.375f, 0.5f));
     if constexpr (NB_EX_LAZY) return ff{y0, corr};
     else return ff_renorm(y0, corr);
+}
+
+// A positive double y in [2^-74, 2^127] as a float pair, from its bits on the
+// integer pipe (no FP64 instruction): hi = the top 24 significant bits
+// (truncated), lo = the remaining 29 bits rounded to a float.
+__device__ __forceinline__ ff ff_from_pos_double(double y) {
+    const int hi = __double2hiint(y);
+    const int lo = __double2loint(y);
+    const float yh = __int_as_float((int)__funnelshift_l((unsigned)lo, (unsigned)(hi - 0x38000000), 3));
+    const float scale = __int_as_float(((hi & 0x7ff00000) - (948 << 20)) << 3);  // 2^(E - 1075)
+    const float yl = __fmul_rn(__uint2float_rn((unsigned)lo & 0x1fffffffu), scale);
+    return ff{yh, yl};
 }
 
 // a.b, unnormalised (hi + lo with every error term in lo)

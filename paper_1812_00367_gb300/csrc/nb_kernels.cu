@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(kSelTPB) k_predict(const Dev d, int also64, in
             w.q[2] = make_double2(vp[0], vp[1]);
             w.q[3] = make_double2(vp[2], ap[0]);
             w.q[4] = make_double2(ap[1], ap[2]);
+            j64_set_mass_split(w, m);
             d.jarr64[jx] = w;
         }
         if (d.precision == NB_EX) {
@@ -281,6 +282,7 @@ __global__ void k_pad(const Dev d) {
         w.q[0] = make_double2(far, far);
         w.q[1] = make_double2(far, 0.0);
         w.q[2] = w.q[3] = w.q[4] = make_double2(0.0, 0.0);
+        j64_set_mass_split(w, 0.0);
         d.jarr64[jx] = w;
         if (d.precision == NB_EX) {
             JEX e;

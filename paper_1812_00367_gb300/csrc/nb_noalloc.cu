@@ -29,7 +29,7 @@ constexpr size_t kNaOffJarr = 0;
 constexpr size_t kNaOffPart = kNaOffJarr + kNaJarrBytes;
 constexpr size_t kNaOffTile = kNaOffPart + kNaPartBytes;
 constexpr size_t kNaOffAux = kNaOffTile + ((kNaTileBytes + 255) / 256) * 256;
-constexpr size_t kNaBytes = kNaOffAux + 256;  // about 5.3 MB in all
+constexpr size_t kNaBytes = kNaOffAux + 256;  // about 5.8 MB in all
 
 struct NaAux {
     int64_t offsets[2];
@@ -64,10 +64,12 @@ __global__ void k_na_prepare(unsigned char *base, const double *jp, int64_t n, i
             w.q[2] = make_double2(jp[3 * n + i], jp[4 * n + i]);
             w.q[3] = make_double2(jp[5 * n + i], jp[6 * n + i]);
             w.q[4] = make_double2(jp[7 * n + i], jp[8 * n + i]);
+            j64_set_mass_split(w, jp[9 * n + i]);
         } else {
             w.q[0] = make_double2(1.0e6, 1.0e6);
             w.q[1] = make_double2(1.0e6, 0.0);
             w.q[2] = w.q[3] = w.q[4] = make_double2(0.0, 0.0);
+            j64_set_mass_split(w, 0.0);
         }
         jarr[i] = w;
     }
