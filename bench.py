@@ -49,8 +49,8 @@ WORKLOAD = (f"Plummer N={N}, equal masses, Henon units, eps={EPS:g}, block steps
 # launch of one ncu capture of this workload (summary and command in
 # profiles/).  It holds for the kernel sources it was taken on (SHA-256 of
 # EVAL_SOURCES below); after any change to them it is reported as null.
-EVAL_TRAFFIC = {"bytes_per_launch": 5930196, "launches": 1520,
-                "sources_sha256": "2daad259d36629a519472f5edb86da7e1417ec485841607abbf300307b637ea1"}
+EVAL_TRAFFIC = {"bytes_per_launch": 6963899, "launches": 1520,
+                "sources_sha256": "4cc249527fb3be7ec47a112ce9b0439b3b8159b49f4c80cd6be6c76313055647"}
 EVAL_SOURCES = ("nb_eval.cuh", "nb_eval_fp64.cu", "nb_step.cuh", "nb_internal.cuh")
 
 
