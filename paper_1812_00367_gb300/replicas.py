@@ -1,8 +1,8 @@
 """Timing bookkeeping for independent replicas on several GPUs.
 
-The method's path needs no data exchange between GPUs in this build (each
-rank integrates its own system); only the benchmark's bookkeeping crosses
-ranks: the slowest rank's time and the sum of the interactions.  Works with
+Replicas exchange no data (each rank integrates its own system); only the
+benchmark's bookkeeping crosses ranks: the slowest rank's time and the sum
+of the interactions.  Works with
 any torch.distributed backend (NCCL on GPUs, gloo on CPU).
 """
 from __future__ import annotations
