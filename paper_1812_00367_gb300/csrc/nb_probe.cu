@@ -13,18 +13,11 @@ constexpr int kThreads = 256;
 // Multiplies and adds that the compiler may not contract into FMAs.
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 // The same products and sums issued as fused multiply-adds (x*b - 0, x*1 + c)
 // with the constants passed at run time, so no compiler can fold them back.
 __device__ __forceinline__ double fma_ptx(double a, double b, double c) {
     double r;
     asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(b), "d"(c));
-    return r;
-}
-__device__ __forceinline__ float fma_ptx(float a, float b, float c) {
-    float r;
-    asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
 }
 
