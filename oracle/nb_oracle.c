@@ -358,6 +358,9 @@ typedef struct {
     double *fa, *fj, *fs, *fp;         /* [n][3], [n] evaluation output */
     int64_t n_underflow;
     int order;                         /* 6 (default) or 4 */
+    /* optional relative perturbation of every evaluation (orc_set_noise) */
+    double noise_a, noise_j, noise_s;
+    uint64_t noise_seed, noise_calls;
 } orc_sim;
 
 size_t orc_sim_sizeof(void) { return sizeof(orc_sim); }
@@ -400,6 +403,57 @@ void orc_free(orc_sim *S)
 }
 
 /*
+ * Perturbed evaluations, for experiments on how accurate the pair arithmetic
+ * must be (the paper's Sec. 2: double precision is needed in the distances
+ * and accelerations).  Off unless orc_set_noise gave a non-zero size; with
+ * all sizes 0 nothing below changes any result.  Each component q of a, jerk
+ * and snap of every evaluated particle is multiplied by (1 + e_q u), u
+ * uniform in [-1, 1), so the relative error of each vector stays <= e_q.
+ * u comes from the counter-based SplitMix64 generator (Steele, Lea & Flood
+ * 2014) keyed by (seed, evaluation number, particle, component): the
+ * perturbation does not depend on the number of threads.
+ */
+static uint64_t splitmix64(uint64_t z)
+{
+    z += 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+static double noise_unit(uint64_t seed, uint64_t call, int64_t i, int q)
+{
+    uint64_t h = splitmix64(seed ^ splitmix64((call << 40) ^ ((uint64_t)i * 16u + (uint64_t)q)));
+    return (double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+static void orc_perturb(orc_sim *S, int64_t na)
+{
+    if (S->noise_a == 0.0 && S->noise_j == 0.0 && S->noise_s == 0.0) return;
+    const uint64_t call = S->noise_calls++;
+    for (int64_t k = 0; k < na; k++) {
+        const int64_t i = S->act[k];
+        for (int d = 0; d < 3; d++) {
+            S->fa[3 * k + d] *= 1.0 + S->noise_a * noise_unit(S->noise_seed, call, i, d);
+            S->fj[3 * k + d] *= 1.0 + S->noise_j * noise_unit(S->noise_seed, call, i, 3 + d);
+            S->fs[3 * k + d] *= 1.0 + S->noise_s * noise_unit(S->noise_seed, call, i, 6 + d);
+        }
+    }
+}
+
+/* Relative sizes of the evaluation perturbation (all 0: none, the default). */
+int orc_set_noise(orc_sim *S, double ea, double ej, double es, uint64_t seed)
+{
+    if (!(ea >= 0.0) || !(ej >= 0.0) || !(es >= 0.0)) return 1;
+    S->noise_a = ea;
+    S->noise_j = ej;
+    S->noise_s = es;
+    S->noise_seed = seed;
+    S->noise_calls = 0;
+    return 0;
+}
+
+/*
  * Start-up at t = 0 (reading: snap needs the j-particles' accelerations, so
  * the first pass runs with a = 0 and yields a and jerk, the second pass uses
  * that a and yields snap; crackle starts at 0).
@@ -419,6 +473,7 @@ void orc_init(orc_sim *S)
     for (int pass = 0; pass < passes; pass++) {
         orc_predict(n, S->x, S->v, S->a, S->j, S->s, S->c, S->t, 0.0, S->xp, S->vp, S->ap);
         orc_force(n, S->m, S->xp, S->vp, S->ap, S->eps2, n, S->act, S->fa, S->fj, S->fs, S->fp);
+        orc_perturb(S, n);
         for (int64_t i = 0; i < n; i++) {
             for (int d = 0; d < 3; d++) {
                 S->a[3 * i + d] = S->fa[3 * i + d];
@@ -468,6 +523,7 @@ static int64_t orc_block_step4(orc_sim *S, double tn, int64_t na)
     orc_predict4(S->n, S->x, S->v, S->a, S->j, S->t, tn, S->xp, S->vp);
     for (int64_t q = 0; q < 3 * S->n; q++) S->ap[q] = 0.0;
     orc_force(S->n, S->m, S->xp, S->vp, S->ap, S->eps2, na, S->act, S->fa, S->fj, S->fs, S->fp);
+    orc_perturb(S, na);
     for (int64_t k = 0; k < na; k++) {
         const int64_t i = S->act[k];
         double *x = &S->x[3 * i], *v = &S->v[3 * i], *a = &S->a[3 * i];
@@ -507,6 +563,7 @@ int64_t orc_block_step(orc_sim *S, double *t_next_out)
     }
     orc_predict(S->n, S->x, S->v, S->a, S->j, S->s, S->c, S->t, tn, S->xp, S->vp, S->ap);
     orc_force(S->n, S->m, S->xp, S->vp, S->ap, S->eps2, na, S->act, S->fa, S->fj, S->fs, S->fp);
+    orc_perturb(S, na);
     for (int64_t k = 0; k < na; k++) {
         const int64_t i = S->act[k];
         double *x = &S->x[3 * i], *v = &S->v[3 * i], *a = &S->a[3 * i];

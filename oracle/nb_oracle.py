@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+    cmd = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp",
            "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
@@ -86,6 +86,9 @@ def lib():
             L.orc_dt_aarseth.restype = C.c_double
             L.orc_set_order.argtypes = [C.c_void_p, C.c_int]
             L.orc_set_order.restype = C.c_int
+            L.orc_set_noise.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                        C.c_uint64]
+            L.orc_set_noise.restype = C.c_int
             _lib = L
     return _lib
 
@@ -239,6 +242,17 @@ class Sim:
             lib().orc_free(self._buf)
         except Exception:
             pass
+
+    def set_noise(self, ea, ej=None, es=None, seed=1):
+        """Perturb every later evaluation: each component of a, jerk and snap
+        is multiplied by (1 + e u), u uniform in [-1, 1) from a counter-based
+        generator keyed by (seed, evaluation, particle, component).  Sizes 0
+        (the default) leave the method untouched."""
+        ej = ea if ej is None else ej
+        es = ea if es is None else es
+        if lib().orc_set_noise(self._buf, float(ea), float(ej), float(es), int(seed)) != 0:
+            raise ValueError("oracle: noise sizes must be >= 0")
+        return self
 
     def init(self):
         lib().orc_init(self._buf)
