@@ -1,0 +1,231 @@
+"""Per-particle parity of the batched block-step path against the FP64 CPU
+oracle, cluster by cluster, through the C ABI.
+
+The batched path advances many independent clusters together: one block
+scheduler pass per cluster, one planned persistent evaluation launch for the
+whole batch (items fetched dynamically, j-ranges split per cluster), the
+corrector fused into that launch, all replayed from a CUDA graph.  Each
+cluster must follow the oracle's own integration of that cluster alone
+(paper Sec. 2: the Hermite 6th-order scheme; block time steps after Makino
+1991 / Aarseth 2003):
+
+* shared steps (every particle active every step) on an uneven batch, from
+  the start-up to 16 steps, compared particle by particle;
+* block steps from identical states: before each step the oracle is given
+  the GPU's state of the cluster, takes its own step, and the selection
+  (t_next, active set), the corrected positions and velocities, the new a,
+  jerk, snap and potential and the new steps are compared;
+* the full 512-cluster batch (N log-uniform in [256, 16384]): start-up a, jerk,
+  snap, potential on sampled clusters, and the first block step's selection
+  of every cluster against the oracle's scheduler.
+
+Tolerances: a, jerk, snap, potential 1e-12 (FP64) and 1e-10 (EX), the
+stated bounds of the pair evaluation.
+"""
+import numpy as np
+import pytest
+
+from paper_1812_00367_gb300 import ic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "ex": 1e-10}
+# shared-step sizes: single and pair clusters, a j-tile -1/+1, several tiles
+# with a ragged tail, and the largest size of the 512-cluster workload
+SHARED_SIZES = [1, 2, 63, 65, 4097, 16384, 300, 1000]
+BLOCK_SIZES = [1, 2, 63, 65, 700, 4097, 300, 1500, 129]
+
+
+@pytest.fixture(scope="module")
+def nb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_00367_gb300 import build as nbbuild
+    nbbuild.build()
+    from paper_1812_00367_gb300 import nb as nbmod
+    nbmod.load()
+    return nbmod
+
+
+def rel_rows(got, ref):
+    num = np.linalg.norm(got - ref, axis=-1)
+    den = np.linalg.norm(ref, axis=-1)
+    return np.where(den > 0, num / np.where(den > 0, den, 1.0), num)
+
+
+def rel_pot(got, ref):
+    den = np.abs(ref)
+    return np.where(den > 0, np.abs(got - ref) / np.where(den > 0, den, 1.0), np.abs(got - ref))
+
+
+def oracle_on_state(oracle, st, lo, hi, eps, **kw):
+    """An oracle simulation of particles [lo, hi) holding exactly the given
+    state (no start-up of its own)."""
+    o = oracle.Sim(st["m"][lo:hi], st["x"][lo:hi], st["v"][lo:hi], eps=eps, **kw)
+    for f in ("a", "j", "s", "c"):
+        getattr(o, f)[:] = st[f][lo:hi]
+    for f in ("t", "dt", "pot"):
+        getattr(o, f)[:] = st[f][lo:hi]
+    return o
+
+
+def check_startup(st, ref, lo, hi, tol, label):
+    for f in ("a", "j", "s"):
+        e = rel_rows(st[f][lo:hi], getattr(ref, f))
+        assert e.max() <= tol, f"{label} start-up {f}: {e.max():.3e}"
+    e = rel_pot(st["pot"][lo:hi], ref.pot)
+    assert e.max() <= tol, f"{label} start-up pot: {e.max():.3e}"
+
+
+# ------------------------------------------------------- shared steps
+@pytest.fixture(scope="module")
+def shared_reference(oracle, trajectory_envelope):
+    """The oracle's start-up and 16 shared steps of every cluster alone, with
+    the trajectory envelopes of evaluation perturbations at the FP64 and EX
+    bounds."""
+    eps, h = 1e-4, 1.0 / 256
+    batch = ic.plummer_batch(sizes=SHARED_SIZES, seed=31)
+    refs = []
+    for c in range(len(SHARED_SIZES)):
+        lo, hi = batch.offsets[c], batch.offsets[c + 1]
+        args = (batch.m[lo:hi], batch.x[lo:hi], batch.v[lo:hi])
+        r = oracle.Sim(*args, eps=eps, dt_min=h, dt_max=h).init()
+        start = {f: getattr(r, f).copy() for f in ("a", "j", "s", "pot")}
+        env = {}
+        for prec, level in TOL.items():
+            xr, vr, ex, ev = trajectory_envelope(*args, eps, h, 16, level)
+            env[prec] = (ex, ev)
+        refs.append((start, xr, vr, env))
+    return batch, eps, h, refs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "ex"])
+def test_uneven_batch_shared_steps_vs_oracle(nb, shared_reference, precision):
+    """Start-up a, jerk, snap, potential at the evaluation bound; after 16
+    shared steps every particle within 2e-14 + 4 x the oracle's own
+    deviation under evaluation perturbations at that bound (close pairs
+    poorly resolved by the 1/256 step amplify any difference: the n = 4097
+    cluster holds a pair whose positions move by ~1e-10 under 1e-12
+    perturbations, or under a 1-ulp change of the initial state)."""
+    batch, eps, h, refs = shared_reference
+    sim = nb.Simulation(batch.m, batch.x, batch.v, eps=eps, precision=precision,
+                        offsets=batch.offsets, dt_min=h, dt_max=h)
+    st0 = sim.state_numpy()
+    tol = TOL[precision]
+    for c, (start, _, _, _) in enumerate(refs):
+        lo, hi = batch.offsets[c], batch.offsets[c + 1]
+        for f in ("a", "j", "s"):
+            e = rel_rows(st0[f][lo:hi], start[f])
+            assert e.max() <= tol, f"cluster {c} (n={hi - lo}) start-up {f}: {e.max():.3e}"
+        e = rel_pot(st0["pot"][lo:hi], start["pot"])
+        assert e.max() <= tol, f"cluster {c} start-up pot: {e.max():.3e}"
+    steps, inter = sim.run(16 * h)
+    assert steps == 16 * len(SHARED_SIZES)
+    n_tot = float(sum(k * (k - 1) for k in SHARED_SIZES))
+    assert inter == pytest.approx(16 * n_tot)
+    st = sim.state_numpy()
+    assert np.all(st["t"] == 16 * h)
+    worst = []
+    for c, (_, xr, vr, env) in enumerate(refs):
+        lo, hi = batch.offsets[c], batch.offsets[c + 1]
+        env_x, env_v = env[precision]
+        ex = rel_rows(st["x"][lo:hi], xr)
+        ev = rel_rows(st["v"][lo:hi], vr)
+        worst.append((c, hi - lo, float(ex.max()), float(env_x.max()), float(ev.max()),
+                      float(env_v.max())))
+        bad_x = np.nonzero(ex > 2e-14 + 4 * env_x)[0]
+        bad_v = np.nonzero(ev > 2e-14 + 4 * env_v)[0]
+        assert bad_x.size == 0, (precision, c, bad_x[:8], ex[bad_x[:8]], env_x[bad_x[:8]])
+        assert bad_v.size == 0, (precision, c, bad_v[:8], ev[bad_v[:8]], env_v[bad_v[:8]])
+    print(f"\n{precision} shared steps per cluster (c, n, max x err, max x envelope, "
+          f"max v err, max v envelope): {worst}")
+    sim.close()
+
+
+# ----------------------------------------- block steps, identical states
+@pytest.mark.parametrize("precision", ["fp64", "ex"])
+def test_block_steps_match_oracle_step_by_step(nb, oracle, precision):
+    eps = 1e-4
+    batch = ic.plummer_batch(sizes=BLOCK_SIZES, seed=32)
+    sim = nb.Simulation(batch.m, batch.x, batch.v, eps=eps, precision=precision,
+                        offsets=batch.offsets)
+    tol = TOL[precision]
+    xtol, vtol = (1e-14, 1e-13) if precision == "fp64" else (1e-12, 1e-11)
+    n_active_seen = []
+    for step in range(8):
+        pre = sim.state_numpy()
+        tn_min, na_tot = sim.step()
+        post = sim.state_numpy()
+        na_sum, tn_seen = 0, []
+        for c in range(len(BLOCK_SIZES)):
+            lo, hi = batch.offsets[c], batch.offsets[c + 1]
+            ref = oracle_on_state(oracle, pre, lo, hi, eps)
+            tn_c, act = ref.select()
+            moved = np.nonzero(post["t"][lo:hi] != pre["t"][lo:hi])[0]
+            # the scheduler: exact selection, in index order
+            np.testing.assert_array_equal(moved, act, err_msg=f"step {step} cluster {c} active set")
+            assert np.all(post["t"][lo:hi][act] == tn_c)
+            na_sum += len(act)
+            tn_seen.append(tn_c)
+            ref.step()
+            for f, tl in (("x", xtol), ("v", vtol)):
+                e = rel_rows(post[f][lo:hi][act], getattr(ref, f)[act])
+                assert e.max(initial=0.0) <= tl, f"step {step} cluster {c} {f}: {e.max():.3e}"
+            for f in ("a", "j", "s"):
+                e = rel_rows(post[f][lo:hi][act], getattr(ref, f)[act])
+                assert e.max(initial=0.0) <= tol, f"step {step} cluster {c} {f}: {e.max():.3e}"
+            e = rel_pot(post["pot"][lo:hi][act], ref.pot[act])
+            assert e.max(initial=0.0) <= tol, f"step {step} cluster {c} pot: {e.max():.3e}"
+            # new steps: a criterion landing within rounding of a power of two
+            # may quantise either way (rare)
+            mism = np.count_nonzero(post["dt"][lo:hi][act] != ref.dt[act])
+            assert mism <= max(1, len(act) // 500), (step, c, mism)
+            # untouched particles stay bit-identical
+            idle = np.setdiff1d(np.arange(hi - lo), act)
+            for f in ("x", "v", "a", "t", "dt"):
+                np.testing.assert_array_equal(post[f][lo:hi][idle], pre[f][lo:hi][idle])
+        assert na_tot == na_sum and tn_min == min(tn_seen)
+        n_active_seen.append(na_sum)
+    assert max(n_active_seen) >= 1
+    sim.close()
+
+
+# ------------------------------------------- the 512-cluster workload
+@pytest.mark.parametrize("precision", ["fp64", "ex"])
+def test_512_cluster_batch_startup_and_selection(nb, oracle, precision):
+    eps = 1e-4
+    batch = ic.plummer_batch(512, seed=1)
+    sizes = batch.sizes
+    sim = nb.Simulation(batch.m, batch.x, batch.v, eps=eps, precision=precision,
+                        offsets=batch.offsets)
+    st0 = sim.state_numpy()
+    # start-up on sampled clusters: the largest, the smallest and six others
+    order = np.argsort(sizes)
+    rng = np.random.default_rng(512)
+    sample = sorted({int(order[-1]), int(order[0]),
+                     *rng.choice(len(sizes), 6, replace=False).tolist()})
+    for c in sample:
+        lo, hi = batch.offsets[c], batch.offsets[c + 1]
+        ref = oracle.Sim(batch.m[lo:hi], batch.x[lo:hi], batch.v[lo:hi], eps=eps).init()
+        check_startup(st0, ref, lo, hi, TOL[precision], f"{precision} cluster {c} (n={hi - lo})")
+    # one block step of every cluster: its selection against the oracle's
+    # scheduler on the same state
+    tn_min, na_tot = sim.step()
+    post = sim.state_numpy()
+    na_sum = 0
+    for c in range(len(sizes)):
+        lo, hi = batch.offsets[c], batch.offsets[c + 1]
+        ref = oracle_on_state(oracle, st0, lo, hi, eps)
+        tn_c, act = ref.select()
+        moved = np.nonzero(post["t"][lo:hi] != st0["t"][lo:hi])[0]
+        np.testing.assert_array_equal(moved, act, err_msg=f"cluster {c} active set")
+        assert np.all(post["t"][lo:hi][act] == tn_c), c
+        na_sum += len(act)
+        if c in sample:
+            ref.step()
+            for f in ("a", "j", "s"):
+                e = rel_rows(post[f][lo:hi][act], getattr(ref, f)[act])
+                assert e.max(initial=0.0) <= TOL[precision], (c, f, e.max())
+    assert na_sum == na_tot
+    sim.close()

@@ -249,11 +249,18 @@ def test_init_parity(nb, oracle, precision):
 
 
 # -------------------------------------------------- shared-step trajectory
-def test_shared_steps_plummer_1024(nb, oracle):
+def test_shared_steps_plummer_1024(nb, oracle, trajectory_envelope):
     """Plummer N=1024, eps=1e-4, shared dt=1/256, 16 steps: per-particle
-    trajectory parity plus energy / momentum bookkeeping."""
+    trajectory parity plus energy / momentum bookkeeping.
+
+    Tolerance per particle: 2e-14 (a few ulps per step of the corrector's
+    rounding) plus 4 times the oracle's own deviation when each of its
+    evaluations carries relative errors up to 1e-12 (the FP64 evaluation
+    bound).  Close pairs that a 1/256 step resolves poorly amplify any such
+    difference (here particles 643 and 187, to about 1e-13)."""
     n, eps, h = 1024, 1e-4, 1.0 / 256
     m, x, v = ic.plummer(n, seed=1)
+    xr, vr, env_x, env_v = trajectory_envelope(m, x, v, eps, h, 16, 1e-12)
     ref = oracle.Sim(m, x, v, eps=eps, dt_min=h, dt_max=h).init()
     e0 = ref.energy(0.0)
     sim = nb.Simulation(m, x, v, eps=eps, precision="fp64", dt_min=h, dt_max=h)
@@ -262,12 +269,20 @@ def test_shared_steps_plummer_1024(nb, oracle):
         tn, na = sim.step()
         assert na == n
     ref.run(16 * h)
+    np.testing.assert_array_equal(ref.x, xr)
     got = sim.state_numpy()
     assert np.all(got["t"] == 16 * h)
     ex = rel_rows(got["x"], ref.x)
     ev = rel_rows(got["v"], ref.v)
-    assert np.median(ex) < 1e-12 and ex.max() < 1e-8, (np.median(ex), ex.max())
-    assert np.median(ev) < 1e-12 and ev.max() < 1e-7, (np.median(ev), ev.max())
+    wx, wv = np.argsort(-ex)[:5], np.argsort(-ev)[:5]
+    print(f"\nconfig-1 trajectory: x max {ex.max():.3e} (particles {wx.tolist()}: {ex[wx]}, "
+          f"envelope {env_x[wx]}), v max {ev.max():.3e} (particles {wv.tolist()}: {ev[wv]}, "
+          f"envelope {env_v[wv]})")
+    bad_x = np.nonzero(ex > 2e-14 + 4 * env_x)[0]
+    bad_v = np.nonzero(ev > 2e-14 + 4 * env_v)[0]
+    assert bad_x.size == 0, (bad_x[:8], ex[bad_x[:8]], env_x[bad_x[:8]])
+    assert bad_v.size == 0, (bad_v[:8], ev[bad_v[:8]], env_v[bad_v[:8]])
+    assert np.median(ex) < 1e-15 and np.median(ev) < 1e-14
     g1 = sim.energy(16 * h)
     e1 = ref.energy(16 * h)
     E0, E1 = g0[0] + g0[1], g1[0] + g1[1]
