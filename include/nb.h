@@ -279,11 +279,14 @@ nb_status nb_autotune(nb_ctx *ctx, const char *cache_path);
  *   stream   : cudaStream_t (NULL = legacy default); the call synchronises it
  *              to read its error word
  * The first call on a device looks up the array's device address with that
- * device current (make that first call before any stream capture).  All
- * calls share the array: calls that overlap on the GPU (other streams,
- * threads or processes sharing the library) race and must be serialised by
- * the caller.  Errors: NB_EINVAL (sizes, NULL pointers, an index outside
- * [0, n): that entry is skipped and reported), NB_ECUDA, NB_ETIMEOUT;
+ * device current (make that first call before any stream capture).  Every
+ * call copies its error word to the host and synchronises `stream` before
+ * it returns.  All calls share the array: calls that overlap on the GPU
+ * (other streams, threads or processes sharing the library) race and must
+ * be serialised by the caller.  Errors: NB_EINVAL (sizes, NULL pointers, an
+ * index outside [0, n): that entry is skipped, its ten outputs are 0, the
+ * other entries are evaluated and the call reports the bad index), NB_ECUDA
+ * (also for a CUDA error already pending when the call starts), NB_ETIMEOUT;
  * messages through nb_last_error(NULL).
  */
 nb_status nb_evaluate_noalloc(const double *jpred, int64_t n, double eps, const int32_t *active,

@@ -9,6 +9,7 @@
 // it.  Every call reuses the same arena, so calls that overlap on the GPU
 // race; each call clears what must start at zero (tile counters, error word).
 #include <mutex>
+#include <string>
 
 #include "nb_eval.cuh"
 
@@ -46,7 +47,8 @@ struct DevSlot {
 std::mutex g_na_mutex;
 DevSlot g_na_slots[128];
 
-// Pack the caller's [10][n] predicted values into 80-byte j entries, pad to
+// Pack the caller's [10][n] predicted values into J64 entries (96 bytes:
+// position, mass, velocity, acceleration and the mass as a float pair), pad to
 // whole 64-particle tiles with zero-mass particles far away, clear the tile
 // counters and the error word, and write the one-cluster offsets.
 __global__ void k_na_prepare(unsigned char *base, const double *jp, int64_t n, int64_t npad,
@@ -143,9 +145,21 @@ extern "C" nb_status nb_evaluate_noalloc(const double *jpred, int64_t n, double 
     if (split > 1 && (int64_t)tiles * split * per_item > cap)
         split = cap / (per_item * tiles) > 1 ? cap / (per_item * tiles) : 1;
 
-    k_na_prepare<<<(unsigned)cdiv(ntj * kTJ, 256), 256, 0, st>>>(slot.base, jpred, n, ntj * kTJ,
-                                                                  tiles);
+    // an error left pending by earlier, unrelated work is reported as such,
+    // not as a failure of this call's launches
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_global_error((std::string("nb_evaluate_noalloc: CUDA error pending before the call: ") +
+                          cudaGetErrorString(e)).c_str());
+        return NB_ECUDA;
+    }
+    // entries whose index is rejected are skipped by the kernel: they read 0
+    e = cudaMemsetAsync(out, 0, sizeof(double) * 10 * (size_t)n_active, st);
+    if (e == cudaSuccess) {
+        k_na_prepare<<<(unsigned)cdiv(ntj * kTJ, 256), 256, 0, st>>>(slot.base, jpred, n,
+                                                                      ntj * kTJ, tiles);
+        e = cudaGetLastError();
+    }
     NaAux *aux = reinterpret_cast<NaAux *>(slot.base + kNaOffAux);
     Dev d{};
     d.n = n;
