@@ -24,7 +24,8 @@ extern "C" {
  *                 instruction rate so it compares with the DFMA figure;
  *                 4: the same stream with its multiplies and adds issued as
  *                 FMAs (x*b - 0, x*1 + c); 5: DADD only; 6: DMUL only;
- *                 others -> NB_EINVAL
+ *                 7: packed two-lane FP32 FMA (fma.rn.f32x2), 4 flops
+ *                 per instruction; others -> NB_EINVAL
  *   iters       : FMA iterations per chain (>= 1), e.g. 4096
  *   stream      : cudaStream_t (NULL = legacy default)
  *   flops_per_s : HOST out, 2 flops per FMA

@@ -786,9 +786,9 @@ nb_status nb_autotune(nb_ctx *ctx, const char *cache_path) {
     std::vector<int32_t> h_act(ncl);
     for (int64_t k = 0; k < ncl; ++k) h_act[k] = (int32_t)(ctx->h_offsets[cmax] + k);
     e = cudaMemcpy(d_act, h_act.data(), ncl * sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int G = ctx->grid_eval;
     const int64_t targets[] = {G / 2, G, 2LL * G, 4LL * G, 8LL * G, 16LL * G};
     const int gls[] = {1, 2, 4, 8, 16, 32};
@@ -809,13 +809,13 @@ nb_status nb_autotune(nb_ctx *ctx, const char *cache_path) {
                 plan_direct(ctx, cmax, A, g2, sp, tl, skm);
                 float ms_best = 1e30f;
                 for (int rep = 0; rep < reps; ++rep) {
-                    cudaEventRecord(e0, ctx->stream);
+                    if ((e = cudaEventRecord(e0, ctx->stream)) != cudaSuccess) break;
                     st = eval_direct(ctx, cmax, d_act, A, d_out, g2, sp, tl, skm);
-                    cudaEventRecord(e1, ctx->stream);
                     if (st != NB_OK) break;
-                    e = cudaEventSynchronize(e1);
+                    if ((e = cudaEventRecord(e1, ctx->stream)) != cudaSuccess) break;
+                    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
                     float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
+                    if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
                     ms_best = std::min(ms_best, ms);
                 }
                 if (st != NB_OK || e != cudaSuccess) break;
@@ -831,8 +831,8 @@ nb_status nb_autotune(nb_ctx *ctx, const char *cache_path) {
         // buckets above the largest timed one reuse its choice
         for (int b2 = b + 1; b2 < kBuckets; ++b2) ctx->table[b2] = bestE;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     cudaFree(d_act);
     cudaFree(d_out);
     if (st != NB_OK) return st;

@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
                 if constexpr (MODE == kModePot) {
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact_pot(me, tl[k], jbase + k == ji, eps2, acc);
-                } else if constexpr (P == NB_EX && is_order4_mode(MODE)) {
+                } else if constexpr (P == NB_EX && uses_order4_terms(MODE)) {
 #pragma unroll 1
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact4(me, tl[k], jbase + k == ji, eps2, eps2f, acc, eps2ff);
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
 #pragma unroll 1
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact(me, tl[k], jbase + k == ji, eps2, eps2f, acc, eps2ff);
-                } else if constexpr (is_order4_mode(MODE)) {
+                } else if constexpr (uses_order4_terms(MODE)) {
 #pragma unroll kEvalUnroll
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact4(me, tl[k], jbase + k == ji, eps2, eps2f, acc);

@@ -203,6 +203,11 @@ enum EvalMode {
     kModeOut4 = 5, kModeStep4 = 6, kModeInit4 = 7
 };
 constexpr bool is_order4_mode(int mode) { return mode >= kModeOut4; }
+// Modes that sum only acceleration, jerk and potential (the 4th-order pair
+// terms): the 4th-order modes, and the first start-up pass of the 6th-order
+// scheme, whose only output that survives is the acceleration (pass 2 needs
+// it for the relative accelerations; it recomputes a and jerk with snap).
+constexpr bool uses_order4_terms(int mode) { return is_order4_mode(mode) || mode == kModeInit1; }
 
 // ---------------------------------------------------------- small helpers
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -68,6 +68,67 @@ __global__ void __launch_bounds__(kThreads) k_fma(T *sink, int64_t iters, T b, T
     sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Packed two-lane FP32 FMA (fma.rn.f32x2, sm_100 and later): each chain is a
+// pair of floats in one 64-bit register, one instruction per chain and step.
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__global__ void __launch_bounds__(kThreads) k_fma2(float *sink, int64_t iters, float b, float c) {
+    unsigned long long acc[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) acc[k] = pack2((float)(threadIdx.x + k), (float)k);
+    const unsigned long long bb = pack2(b, b), cc = pack2(c, c);
+    for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k)
+            asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(acc[k]) : "l"(bb), "l"(cc));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[k]));
+        s += lo + hi;
+    }
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+nb_status run_fma2(int64_t iters, cudaStream_t st, double *fps, double *sec) {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NB_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NB_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fma2, kThreads, 0) != cudaSuccess)
+        return NB_ECUDA;
+    const int blocks = sms * (occ > 0 ? occ : 1);
+    float *sink = nullptr;
+    if (cudaMalloc(&sink, sizeof(float) * blocks * kThreads) != cudaSuccess) return NB_ECUDA;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        k_fma2<<<blocks, kThreads, 0, st>>>(sink, iters / 8 + 1, 0.999999f, 1e-3f);  // warm-up
+        e = cudaEventRecord(e0, st);
+    }
+    if (e == cudaSuccess) {
+        k_fma2<<<blocks, kThreads, 0, st>>>(sink, iters, 0.999999f, 1e-3f);
+        e = cudaEventRecord(e1, st);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess || ms <= 0.f) return NB_ECUDA;
+    // two lanes x 2 flops per instruction
+    const double flops = 4.0 * kChains * (double)iters * (double)blocks * kThreads;
+    if (fps) *fps = flops / (ms * 1e-3);
+    if (sec) *sec = ms * 1e-3;
+    return NB_OK;
+}
+
 template <typename T, int MODE>
 nb_status run(int64_t iters, cudaStream_t st, double *fps, double *sec) {
     int dev = 0, sms = 0, occ = 0;
@@ -114,6 +175,7 @@ extern "C" nb_status nb_probe_fma_peak(int32_t precision, int64_t iters, void *s
     case 4: return run<double, kMixFma>(iters, st, flops_per_s, seconds);
     case 5: return run<double, kAdd>(iters, st, flops_per_s, seconds);
     case 6: return run<double, kMul>(iters, st, flops_per_s, seconds);
+    case 7: return run_fma2(iters, st, flops_per_s, seconds);
     default: break;
     }
     return NB_EINVAL;
