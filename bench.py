@@ -280,6 +280,9 @@ def gpu_arm(args, ws, rank, local):
             kern[prec] = {f"A={a}": eval_rate(nb, torch, dev, m, x, v, prec, a, 2 if a == N else 10)
                           for a in (1024, N)}
     e2e_val, state_bytes = (e2e_run(k2, args.warmup) if not args.only_fp64 else (None, 0))
+    # configurations 1, 3, 4, 5 beside the headline (rank 0 of a replica run)
+    configs, samples = (config_suite(nb, torch, dev, flush, peak64, ic)
+                        if not (args.only_fp64 or args.no_configs) and rank == 0 else (None, None))
 
     eval_avg_ms = r64["eval_ms"] / max(r64["eval_launches"], 1)
     # algorithmic flops of the evaluation launches in the timed region
@@ -298,6 +301,9 @@ def gpu_arm(args, ws, rank, local):
                    "l2": "flushed (256 MB write) before each timed step",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "plan_table": "default" if args.no_autotune else "nb_autotune before timing",
+                   "potential": "the FP64 path sums the potential m/r in float-float on the FP32 "
+                                "pipe (about 2^-45 per 64-pair tile, FP64 across tiles); a, jerk "
+                                "and snap are all FP64",
                    "seed": SEED},
         "gflops_79": value * FLOPS_PER_INTERACTION / 1e9,
         "fp64_fma_peak_tflops_measured": peak64 / 1e12,
@@ -333,8 +339,12 @@ def gpu_arm(args, ws, rank, local):
         "wall_s_timed_region": t_wall,
         "dt_underflows": r64["underflows"],
     }
+    if configs is not None:
+        out["configs"] = configs
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if samples is not None:
+            out["cpu_baseline"]["configs"] = cpu_config_checks(samples)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -365,6 +375,236 @@ def eval_rate(nb, torch, dev, m, x, v, precision, A, reps, order=6):
     sim.close()
     ms = e0.elapsed_time(e1) / reps
     return {"interactions_per_s": A * (n - 1) / (ms * 1e-3), "ms_per_launch": ms}
+
+
+def _keep_state_sim(nb, m, x, v, a, eps, precision, order=6):
+    """A context over (m, x, v) at t = 0 holding the given accelerations
+    (they enter the snap terms) with no start-up evaluations of its own."""
+    n = len(m)
+    sim = nb.Simulation(m, x, v, eps=eps, precision=precision, keep_state=True, order=order)
+    st = {"m": m, "x": x, "v": v, "a": a, "j": np.zeros((n, 3)), "s": np.zeros((n, 3)),
+          "c": np.zeros((n, 3)), "t": np.zeros(n), "dt": np.full(n, 2.0 ** -6),
+          "pot": np.zeros(n)}
+    sim.set_state_numpy(st)
+    sim.predict(0.0, out=False)
+    return sim
+
+
+def timed_evals(nb, torch, dev, sim, n, actives, flush, keep_largest=True):
+    """Evaluation-kernel rate of each active-set size: the active particles are
+    spread evenly over the index range; L2 is flushed before every timed
+    launch (CUDA events on the stream around the launches only).  Returns the
+    rates and, for the largest size, its index list and outputs (host)."""
+    stream = torch.cuda.current_stream(dev)
+    res, kept = {}, None
+    for A in actives:
+        idx = np.linspace(0, n - 1, A).astype(np.int32)
+        act = torch.as_tensor(idx, device=dev)
+        o = torch.empty((10, A), dtype=torch.float64, device=dev)
+        nb.nb_evaluate(sim.ctx, 0, act[:min(A, 1024)], min(A, 1024), o)   # warm-up
+        reps = 5 if A <= 4096 else 1
+        ms = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nb.nb_evaluate(sim.ctx, 0, act, A, o)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms += e0.elapsed_time(e1)
+        ms /= reps
+        res[f"A={A}"] = {"interactions_per_s": A * (n - 1) / (ms * 1e-3), "ms_per_launch": ms}
+        if keep_largest and A == max(actives):
+            kept = (idx, o.cpu().numpy())
+    sim.sync()
+    return res, kept
+
+
+def config_suite(nb, torch, dev, flush, peak64, ic):
+    """Configurations 1, 3, 4 and 5 beside the headline (configuration 2):
+    GPU rates, each FP64 rate also as a fraction of the measured DFMA peak.
+    Returns (results, samples): the samples are what the CPU-baseline leg
+    evaluates with the oracle (timed) and compares."""
+    out, samples = {}, {}
+    rng = np.random.default_rng(2024)
+
+    # -- configuration 1: Plummer N=1024, eps 1e-4, one full evaluation and 16
+    # shared steps of 1/256 (FP64)
+    n1, eps1, h1 = 1024, 1e-4, 1.0 / 256
+    m1, x1, v1 = ic.plummer(n1, seed=1)
+    r_eval = eval_rate(nb, torch, dev, m1, x1, v1, "fp64", n1, 50)
+    sim = nb.Simulation(m1, x1, v1, eps=eps1, precision="fp64", dt_min=h1, dt_max=h1)
+    E0 = sim.energy(0.0)
+    flush.zero_()
+    steps, inter, sec = _timed_run(sim, torch, dev, 16 * h1)
+    E1 = sim.energy(16 * h1)
+    st1 = sim.state_numpy()
+    sim.close()
+    out["c1_plummer_n1024"] = {
+        "workload": "Plummer N=1024, eps=1e-4, FP64: one all-active evaluation; 16 shared steps dt=1/256",
+        "eval_interactions_per_s": r_eval["interactions_per_s"],
+        "eval_frac_of_fp64_peak": r_eval["interactions_per_s"] * FLOPS_PER_INTERACTION / peak64,
+        "shared_steps": steps, "ms_per_shared_step": 1e3 * sec / steps,
+        "step_interactions_per_s": inter / sec,
+        "rel_energy_change": abs((E1[0] + E1[1]) - (E0[0] + E0[1])) / abs(E0[0] + E0[1]),
+        "dP": float(np.linalg.norm(E1[2] - E0[2]))}
+    samples["c1"] = {"m": m1, "x0": x1, "v0": v1, "eps": eps1, "h": h1, "x": st1["x"],
+                     "v": st1["v"], "E0": E0[0] + E0[1], "E1": E1[0] + E1[1]}
+
+    # -- configuration 3: Plummer N=2^20, Kroupa masses, eps 1e-5: a 1/16
+    # slice of the full evaluation in FP64, the full evaluation in EX and FP32
+    n3, eps3 = 1 << 20, 1e-5
+    m3, x3, v3 = ic.plummer(n3, seed=3, masses=ic.kroupa_masses(n3, seed=3))
+    a3 = rng.normal(size=(n3, 3)) * 0.3
+    c3 = {"workload": "Plummer N=2^20, Kroupa-like masses (0.1-100), eps=1e-5: all-active "
+                      "evaluation (FP64: 65536 active, 1/16 of it)"}
+    samples["c3"] = {"m": m3, "x": x3, "v": v3, "a": a3, "eps": eps3, "gpu": {}}
+    for prec in ("fp64", "ex", "fp32"):
+        A = 65536 if prec == "fp64" else n3
+        sim = _keep_state_sim(nb, m3, x3, v3, a3, eps3, prec)
+        rates, (idx, o) = timed_evals(nb, torch, dev, sim, n3, (A,), flush)
+        sim.close()
+        c3[prec] = rates
+        pick = np.sort(rng.choice(len(idx), 256, replace=False))
+        samples["c3"]["gpu"][prec] = (idx[pick], o[:, pick])
+    c3["fp64_frac_of_fp64_peak"] = (c3["fp64"]["A=65536"]["interactions_per_s"]
+                                   * FLOPS_PER_INTERACTION / peak64)
+    c3["ex_speedup_vs_fp64"] = (c3["ex"][f"A={n3}"]["interactions_per_s"]
+                                / c3["fp64"]["A=65536"]["interactions_per_s"])
+    out["c3_kroupa_plummer_n2p20"] = c3
+    del m3, x3, v3
+
+    # -- configuration 4: 512 Plummer clusters, N log-uniform in [256, 16384],
+    # eps 1e-4: start-up, block steps to t = 1/256 (untimed), then a timed
+    # window of 1/256 of block steps of every cluster, graph-replayed
+    batch = ic.plummer_batch(512, seed=1)
+    c4 = {"workload": "512 Plummer clusters, N log-uniform in [256, 16384] (sum "
+                      f"{int(batch.offsets[-1])}), eps=1e-4, own block steps per cluster; timed "
+                      "window t = 1/256 .. 2/256", "clusters": 512,
+          "n_total": int(batch.offsets[-1])}
+    sizes = batch.sizes
+    order = np.argsort(sizes)
+    csample = sorted({int(order[-1]), int(order[0]), *rng.choice(512, 6, replace=False).tolist()})
+    samples["c4"] = {"batch": batch, "eps": 1e-4, "clusters": csample, "gpu": {}}
+    for prec in ("fp64", "ex"):
+        sim = nb.Simulation(batch.m, batch.x, batch.v, eps=1e-4, eta=ETA, dt_min=DT_MIN,
+                            dt_max=DT_MAX, precision=prec, offsets=batch.offsets)
+        st = sim.state_numpy()
+        samples["c4"]["gpu"][prec] = {f: st[f] for f in ("a", "j", "s", "pot")}
+        t0, t1 = 1.0 / 256, 2.0 / 256
+        sim.run(t0)
+        e0 = sim.energy_all(t0)[:, :2].sum(axis=1)
+        flush.zero_()
+        steps, inter, sec = _timed_run(sim, torch, dev, t1)
+        e1 = sim.energy_all(t1)[:, :2].sum(axis=1)
+        sim.close()
+        drift = np.abs(e1 - e0) / np.abs(e0) / (t1 - t0)
+        c4[prec] = {"interactions_per_s": inter / sec, "seconds": sec, "cluster_block_steps": steps,
+                    "interactions": inter,
+                    "energy_drift_per_time_max": float(drift.max()),
+                    "energy_drift_per_time_median": float(np.median(drift))}
+    c4["fp64_frac_of_fp64_peak"] = c4["fp64"]["interactions_per_s"] * FLOPS_PER_INTERACTION / peak64
+    c4["ex_speedup_vs_fp64"] = c4["ex"]["interactions_per_s"] / c4["fp64"]["interactions_per_s"]
+    out["c4_batched_512"] = c4
+
+    # -- configuration 5: two Hernquist spheres of 2^21 each, eps 1e-3:
+    # evaluation of 64, 1024 and 65536 active particles against all 4,194,304
+    m5, x5, v5 = ic.hernquist_merger(1 << 21, seed=5)
+    n5 = len(m5)
+    a5 = rng.normal(size=(n5, 3)) * 0.1
+    c5 = {"workload": "two Hernquist spheres 2 x 2^21 on a parabolic orbit at separation 20, "
+                      "eps=1e-3: A active (evenly spread) against all 4,194,304"}
+    samples["c5"] = {"m": m5, "x": x5, "v": v5, "a": a5, "eps": 1e-3, "gpu": {}}
+    for prec, acts in (("fp64", (64, 1024, 65536)), ("ex", (64, 1024, 65536)),
+                       ("fp32", (65536,))):
+        sim = _keep_state_sim(nb, m5, x5, v5, a5, 1e-3, prec)
+        rates, (idx, o) = timed_evals(nb, torch, dev, sim, n5, acts, flush)
+        sim.close()
+        c5[prec] = rates
+        pick = np.sort(rng.choice(len(idx), 64, replace=False))
+        samples["c5"]["gpu"][prec] = (idx[pick], o[:, pick])
+    c5["fp64_frac_of_fp64_peak"] = {k: r["interactions_per_s"] * FLOPS_PER_INTERACTION / peak64
+                                    for k, r in c5["fp64"].items()}
+    c5["ex_speedup_vs_fp64"] = (c5["ex"]["A=65536"]["interactions_per_s"]
+                                / c5["fp64"]["A=65536"]["interactions_per_s"])
+    out["c5_hernquist_merger_n4194304"] = c5
+    return out, samples
+
+
+def _rel_errs(out, ref):
+    acc, jrk, snp, pot = ref
+    e = {}
+    for name, lo, r in (("a", 0, acc), ("j", 3, jrk), ("s", 6, snp)):
+        d = np.linalg.norm(out[lo:lo + 3].T - r, axis=1) / np.linalg.norm(r, axis=1)
+        e[name] = float(d.max())
+    e["pot"] = float((np.abs(out[9] - pot) / np.abs(pot)).max())
+    return e
+
+
+def cpu_config_checks(samples):
+    """CPU-baseline leg of configurations 1, 3, 4, 5: the oracle, as it stands,
+    on the host cores over a bounded sample of each workload (timed:
+    interactions/s), and the largest relative difference of the GPU's results
+    from the oracle's on that same sample (a, jerk, snap, potential; per
+    arithmetic)."""
+    from oracle import nb_oracle
+    nb_oracle.build()
+    res = {}
+    c = samples["c1"]
+    t0 = time.perf_counter()
+    ref = nb_oracle.Sim(c["m"], c["x0"], c["v0"], eps=c["eps"], dt_min=c["h"], dt_max=c["h"]).init()
+    r0 = ref.energy(0.0)
+    ref.run(16 * c["h"])
+    sec = time.perf_counter() - t0
+    r1 = ref.energy(16 * c["h"])
+    ex = np.linalg.norm(c["x"] - ref.x, axis=1) / np.linalg.norm(ref.x, axis=1)
+    ev = np.linalg.norm(c["v"] - ref.v, axis=1) / np.linalg.norm(ref.v, axis=1)
+    res["c1"] = {"sample": "the whole run: start-up and 16 shared steps",
+                 "interactions_per_s": ref.interactions / sec, "seconds": sec,
+                 "gpu_vs_oracle": {"x_max_rel": float(ex.max()), "v_max_rel": float(ev.max()),
+                                   "x_median_rel": float(np.median(ex)),
+                                   "energy_change_gpu": c["E1"] - c["E0"],
+                                   "energy_change_oracle": (r1[0] + r1[1]) - (r0[0] + r0[1])}}
+    for key in ("c3", "c5"):
+        c = samples[key]
+        idx = next(iter(c["gpu"].values()))[0]
+        errs, sec, ninter = {}, 0.0, 0.0
+        refs = {}
+        for prec, (ix, o) in c["gpu"].items():
+            k = tuple(ix.tolist())
+            if k not in refs:
+                t0 = time.perf_counter()
+                refs[k] = nb_oracle.force(c["m"], c["x"], c["v"], c["a"], c["eps"], active=ix)
+                sec += time.perf_counter() - t0
+                ninter += len(ix) * (len(c["m"]) - 1)
+            errs[prec] = _rel_errs(o, refs[k])
+        res[key] = {"sample": f"{len(idx)} active particles (per arithmetic, from its largest "
+                              f"timed set) against all {len(c['m'])}",
+                    "interactions_per_s": ninter / sec, "seconds": sec,
+                    "gpu_vs_oracle_max_rel": errs}
+    c = samples["c4"]
+    b = c["batch"]
+    errs = {p: {"a": 0.0, "j": 0.0, "s": 0.0, "pot": 0.0} for p in c["gpu"]}
+    sec, ninter = 0.0, 0.0
+    for k in c["clusters"]:
+        lo, hi = b.offsets[k], b.offsets[k + 1]
+        t0 = time.perf_counter()
+        ref = nb_oracle.Sim(b.m[lo:hi], b.x[lo:hi], b.v[lo:hi], eps=c["eps"]).init()
+        sec += time.perf_counter() - t0
+        ninter += ref.interactions
+        for prec, g in c["gpu"].items():
+            for f in ("a", "j", "s"):
+                d = (np.linalg.norm(g[f][lo:hi] - getattr(ref, f), axis=1)
+                     / np.linalg.norm(getattr(ref, f), axis=1))
+                errs[prec][f] = max(errs[prec][f], float(d.max()))
+            d = np.abs(g["pot"][lo:hi] - ref.pot) / np.abs(ref.pot)
+            errs[prec]["pot"] = max(errs[prec]["pot"], float(d.max()))
+    res["c4"] = {"sample": f"start-up (two passes) of {len(c['clusters'])} clusters "
+                           "(the largest, the smallest, six at random)",
+                 "interactions_per_s": ninter / sec, "seconds": sec,
+                 "gpu_vs_oracle_max_rel": errs}
+    return res
 
 
 def eval_case(args):
@@ -597,6 +837,69 @@ def merger_case(args):
     print(json.dumps(out))
 
 
+def merger_window_case(args):
+    """Configuration 5 block steps within a fixed wall-clock window: two
+    Hernquist spheres of 2^21 particles each (parabolic orbit, separation 20),
+    eps = 1e-3, eta = 0.4, steps in [2^-20, 2^-3], in the given arithmetic.
+    Reports the start-up cost separately, then block steps for about
+    --window-seconds: block steps, interactions, the time reached, the
+    evaluation share of the step time (CUDA events around every evaluation
+    launch) and the extrapolation of interactions and time to t = 1 at the
+    window's rate."""
+    import torch
+    from paper_1812_00367_gb300 import build as nbbuild
+    from paper_1812_00367_gb300 import ic, nb
+    nbbuild.build()
+    nb.load()
+    dev = torch.device("cuda", 0)
+    m, x, v = ic.hernquist_merger(1 << 21, seed=5)
+    n = len(m)
+    out = {"case": "merger-window", "n": n, "eps": 1e-3, "precision": args.precision,
+           "window_seconds_target": args.window_seconds}
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sim = nb.Simulation(m, x, v, eps=1e-3, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX,
+                        precision=args.precision, time_eval=True)
+    torch.cuda.synchronize(dev)
+    t_start = time.perf_counter() - t0
+    out["startup_seconds"] = t_start
+    out["startup_interactions"] = 2.0 * n * (n - 1) if sim.order == 6 else 1.0 * n * (n - 1)
+    st = sim.state_numpy()
+    dts = st["dt"]
+    out["startup_dt_histogram_log2"] = {int(k): int(c) for k, c in
+                                        zip(*np.unique(np.log2(dts).astype(int), return_counts=True))}
+    stream = torch.cuda.current_stream(dev)
+    steps_tot, inter_tot, sec_tot, t_reached = 0, 0.0, 0.0, 0.0
+    c0 = sim.counters()
+    chunk = 64
+    while sec_tot < args.window_seconds:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k, inter = sim.run(1.0, chunk)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sec_tot += e0.elapsed_time(e1) * 1e-3
+        steps_tot += k
+        inter_tot += inter
+        if k == 0:
+            break
+    c1 = sim.counters()
+    st = sim.state_numpy()
+    t_reached = float(st["t"].min())
+    eval_s = (c1["eval_ms"] - c0["eval_ms"]) * 1e-3
+    sim.close()
+    out.update({
+        "window_seconds": sec_tot, "block_steps": steps_tot, "interactions": inter_tot,
+        "interactions_per_s": inter_tot / sec_tot, "t_reached": t_reached,
+        "eval_share_of_step_time": eval_s / sec_tot if sec_tot > 0 else None,
+        "eval_interactions_per_s": inter_tot / eval_s if eval_s > 0 else None,
+        "dt_underflows": c1["dt_underflows"],
+        "extrapolated_interactions_to_t1": inter_tot / t_reached if t_reached > 0 else None,
+        "extrapolated_seconds_to_t1": sec_tot / t_reached if t_reached > 0 else None})
+    print(json.dumps(out))
+
+
 def histogram_case(args):
     """Configuration 2 (Plummer N=65536, eps 1e-4, eta 0.4, block steps)
     from start-up to t = 0.25 one block step at a time, FP64: the active-set
@@ -773,6 +1076,7 @@ def cpu_baseline(seconds: float):
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"oracle start-up of the same N={N} Plummer system ({t_init:.1f} s, untimed), "
                       f"then its first {steps} block steps ({dt:.1f} s timed)",
+            "value_single_core": len(act1) * (N - 1) / dt1,
             "init_interactions_per_s": inter0 / t_init,
             "single_core": {"value": len(act1) * (N - 1) / dt1, "cores": 1,
                             "sample": f"evaluation of {len(act1)} active particles against all "
@@ -823,11 +1127,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-interactions", type=float, default=5e8)
     ap.add_argument("--only-fp64", action="store_true", help="headline run only (profiling)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the configuration 1/3/4/5 measurements beside the headline")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default plan table")
     ap.add_argument("--slice", type=float, default=SLICE,
                     help="N-body time per step (a power of two dividing 0.25); shorter for profiling")
     ap.add_argument("--case", choices=["run", "eval", "batched", "config3", "merger", "config2-check",
-                                       "order4", "energy", "histogram"],
+                                       "order4", "energy", "histogram", "merger-window"],
                     default="run")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--batched-target", type=int, default=0,
@@ -845,12 +1151,13 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--energy-seconds", type=float, default=4.0)
     ap.add_argument("--order", type=int, default=6, choices=[4, 6], help="--case eval only")
+    ap.add_argument("--window-seconds", type=float, default=300.0, help="--case merger-window")
     args = ap.parse_args()
     if args.case != "run":
         {"eval": eval_case, "batched": batched_case, "config3": config3_case,
          "merger": merger_case, "config2-check": config2_check,
          "order4": order4_case, "energy": energy_case,
-         "histogram": histogram_case}[args.case](args)
+         "histogram": histogram_case, "merger-window": merger_window_case}[args.case](args)
         return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
