@@ -45,6 +45,7 @@ struct Prec;
 template <>
 struct Prec<NB_FP64> {
     using J = J64;
+    static constexpr int kPerRec = 1;  // particles per record
     struct I {
         double x[3], v[3], a[3];
         double m1, nz;  // -1.0, -0.0 from kernel parameters (see Dev)
@@ -193,90 +194,113 @@ struct Prec<NB_FP64> {
 };
 
 // ======================================================================= EX
+// Float-float pair terms, two j per thread and step like the FP32 path: the
+// record (JEXP) gives both particles' hi and lo parts as two-lane operands
+// and every float-float primitive runs on float2 lanes (ff2).  Sums and
+// products are kept unnormalised wherever the next operation only folds lo
+// into first-order terms (the lazy forms); the accumulators are renormalised
+// once per j-tile.
 template <>
 struct Prec<NB_EX> {
-    using J = JEX;
-    struct I {
-        ff x[3], v[3], a[3];
+    using J = JEXP;
+    static constexpr int kPerRec = 2;
+    struct I {  // the i-particle, both lanes equal
+        ff2 x[3], v[3], a[3];
     };
-    struct Acc {
-        ff a[3], j[3], s[3], p;
+    struct Acc {  // lane l sums the j of parity l
+        ff2 a[3], j[3], s[3], p;
     };
+    static __device__ __forceinline__ ff2 dup(float hi, float lo) { return ff2{f2s(hi), f2s(lo)}; }
     static __device__ __forceinline__ I load_i(const J *jarr, int64_t k) {
-        const J e = jarr[k];
+        const float *f = reinterpret_cast<const float *>(jarr + (k >> 1)) + (k & 1);
         I r;
-        r.x[0] = ff{e.q[0].x, e.q[1].x}; r.x[1] = ff{e.q[0].y, e.q[1].y}; r.x[2] = ff{e.q[0].z, e.q[1].z};
-        r.v[0] = ff{e.q[2].x, e.q[3].x}; r.v[1] = ff{e.q[2].y, e.q[3].y}; r.v[2] = ff{e.q[2].z, e.q[3].z};
-        r.a[0] = ff{e.q[2].w, e.q[3].w}; r.a[1] = ff{e.q[4].x, e.q[4].z}; r.a[2] = ff{e.q[4].y, e.q[4].w};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            r.x[q] = dup(f[2 * q], f[2 * (4 + q)]);
+            r.v[q] = dup(f[2 * (8 + q)], f[2 * (12 + q)]);
+        }
+        r.a[0] = dup(f[2 * 11], f[2 * 15]);
+        r.a[1] = dup(f[2 * 16], f[2 * 18]);
+        r.a[2] = dup(f[2 * 17], f[2 * 19]);
         return r;
     }
     static __device__ __forceinline__ void zero(Acc &c) {
+        const float2 z = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = ff{0.f, 0.f};
-        c.p = ff{0.f, 0.f};
+        for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = ff2{z, z};
+        c.p = ff2{z, z};
     }
-    static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self, double,
-                                                    float, Acc &c, ff eps2) {
-        const float4 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3], q4 = jj.q[4];
-        ff r[3], v[3], a[3];
-        r[0] = ff_sub(ff{q0.x, q1.x}, i.x[0]);
-        r[1] = ff_sub(ff{q0.y, q1.y}, i.x[1]);
-        r[2] = ff_sub(ff{q0.z, q1.z}, i.x[2]);
-        v[0] = ff_sub(ff{q2.x, q3.x}, i.v[0]);
-        v[1] = ff_sub(ff{q2.y, q3.y}, i.v[1]);
-        v[2] = ff_sub(ff{q2.z, q3.z}, i.v[2]);
-        a[0] = ff_sub(ff{q2.w, q3.w}, i.a[0]);
-        a[1] = ff_sub(ff{q4.x, q4.z}, i.a[1]);
-        a[2] = ff_sub(ff{q4.y, q4.w}, i.a[2]);
-        ff r2 = NB_EX_LAZY ? ff_dot3_add_lazy(r, r, eps2) : ff_add(ff_dot3(r, r), eps2);
-        ff m = ff{q0.w, q1.w};
-        if (self) {
-            r2 = ff{1.f, 0.f};
-            m = ff{0.f, 0.f};
-        }
-        const ff y = rsqrt_ff(r2);
-        const ff rv = NB_EX_LAZY ? ff_dot3_lazy(r, v) : ff_dot3(r, v);
-        ff y2, my, q, w, al, ze, al3, be3;
-        if constexpr (NB_EX_LAZY) {
-            y2 = ff_sqr_lazy(y);
-            my = ff_mul_lazy(m, y);
-            q = ff_mul_lazy(my, y2);
-            w = ff_dot3x2_lazy(v, v, r, a);
-            al = ff_mul_lazy(rv, y2);
-            ze = ff_mul_lazy(w, y2);
-            al3 = ff_mul_f_lazy(al, 3.0f);
-            be3 = ff_mul_f_lazy(ff_sum_lazy(ff_sqr_lazy(al), ze), 3.0f);
-        } else {
-            y2 = ff_sqr(y);
-            my = ff_mul(m, y);
-            q = ff_mul(my, y2);
-            w = ff_add(ff_dot3(v, v), ff_dot3(r, a));
-            al = ff_mul(rv, y2);
-            ze = ff_mul(w, y2);
-            al3 = ff_mul_f(al, 3.0f);
-            be3 = ff_mul_f(ff_add(ff_sqr(al), ze), 3.0f);
-        }
-        const ff al6 = ff{2.0f * al3.hi, 2.0f * al3.lo};  // exact
-        if constexpr (NB_EX_LAZY) {
-            ff_add_lazy(c.p, my);
+    // relative positions and velocities, normalised (after cancellation lo
+    // can exceed hi)
+    static __device__ __forceinline__ void rel(const I &i, const J &jj, ff2 r[3], ff2 v[3]) {
+        const float4 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
+        const float4 q4 = jj.q[4], q5 = jj.q[5], q6 = jj.q[6], q7 = jj.q[7];
+        r[0] = ff_sub(ff2{lo2(q0), lo2(q2)}, i.x[0]);
+        r[1] = ff_sub(ff2{hi2(q0), hi2(q2)}, i.x[1]);
+        r[2] = ff_sub(ff2{lo2(q1), lo2(q3)}, i.x[2]);
+        v[0] = ff_sub(ff2{lo2(q4), lo2(q6)}, i.v[0]);
+        v[1] = ff_sub(ff2{hi2(q4), hi2(q6)}, i.v[1]);
+        v[2] = ff_sub(ff2{lo2(q5), lo2(q7)}, i.v[2]);
+    }
+    static __device__ __forceinline__ void exclude_self(bool self0, bool self1, ff2 &r2, ff2 &m) {
+        r2.hi.x = self0 ? 1.f : r2.hi.x;  // selects, not arithmetic
+        r2.lo.x = self0 ? 0.f : r2.lo.x;
+        m.hi.x = self0 ? 0.f : m.hi.x;
+        m.lo.x = self0 ? 0.f : m.lo.x;
+        r2.hi.y = self1 ? 1.f : r2.hi.y;
+        r2.lo.y = self1 ? 0.f : r2.lo.y;
+        m.hi.y = self1 ? 0.f : m.hi.y;
+        m.lo.y = self1 ? 0.f : m.lo.y;
+    }
+    static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self0, bool self1,
+                                                    ff2 eps2, Acc &c) {
+        ff2 r[3], v[3], a[3];
+        rel(i, jj, r, v);
+        a[0] = ff_sub(ff2{hi2(jj.q[5]), hi2(jj.q[7])}, i.a[0]);
+        a[1] = ff_sub(ff2{lo2(jj.q[8]), lo2(jj.q[9])}, i.a[1]);
+        a[2] = ff_sub(ff2{hi2(jj.q[8]), hi2(jj.q[9])}, i.a[2]);
+        ff2 r2 = ff_dot3_add_lazy(r, r, eps2);
+        ff2 m{hi2(jj.q[1]), hi2(jj.q[3])};
+        exclude_self(self0, self1, r2, m);
+        const ff2 y = rsqrt_ff(r2);
+        const ff2 rv = ff_dot3_lazy(r, v);
+        const ff2 y2 = ff_sqr_lazy(y);
+        const ff2 my = ff_mul_lazy(m, y);
+        const ff2 q = ff_mul_lazy(my, y2);
+        const ff2 w = ff_dot3x2_lazy(v, v, r, a);
+        const ff2 al = ff_mul_lazy(rv, y2);
+        const ff2 ze = ff_mul_lazy(w, y2);
+        const ff2 al3 = ff_mul_f_lazy(al, f2s(3.0f));
+        const ff2 be3 = ff_mul_f_lazy(ff_sum_lazy(ff_sqr_lazy(al), ze), f2s(3.0f));
+        const ff2 al6 = ff2{add2(al3.hi, al3.hi), add2(al3.lo, al3.lo)};  // exact
+        ff_add_lazy(c.p, my);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const ff w1 = ff_fnma_lazy(al3, r[k], v[k]);
-                const ff w2 = ff_fnma_lazy(be3, r[k], ff_fnma_lazy(al6, w1, a[k]));
-                ff_fma_acc_lazy(c.a[k], q, r[k]);
-                ff_fma_acc_lazy(c.j[k], q, w1);
-                ff_fma_acc_lazy(c.s[k], q, w2);
-            }
-        } else {
-            c.p = ff_add(c.p, my);
+        for (int k = 0; k < 3; ++k) {
+            const ff2 w1 = ff_fnma_lazy(al3, r[k], v[k]);
+            const ff2 w2 = ff_fnma_lazy(be3, r[k], ff_fnma_lazy(al6, w1, a[k]));
+            ff_fma_acc_lazy(c.a[k], q, r[k]);
+            ff_fma_acc_lazy(c.j[k], q, w1);
+            ff_fma_acc_lazy(c.s[k], q, w2);
+        }
+    }
+    static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self0, bool self1,
+                                                     ff2 eps2, Acc &c) {
+        ff2 r[3], v[3];
+        rel(i, jj, r, v);
+        ff2 r2 = ff_dot3_add(r, r, eps2);
+        ff2 m{hi2(jj.q[1]), hi2(jj.q[3])};
+        exclude_self(self0, self1, r2, m);
+        const ff2 y = rsqrt_ff(r2);
+        const ff2 y2 = ff_sqr_lazy(y);
+        const ff2 my = ff_mul_lazy(m, y);
+        const ff2 q = ff_mul_lazy(my, y2);
+        const ff2 al3 = ff_mul_f_lazy(ff_mul_lazy(ff_dot3(r, v), y2), f2s(3.0f));
+        ff_add_lazy(c.p, my);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const ff w1 = ff_fnma(al3, r[k], v[k]);
-                const ff w2 = ff_fnma(be3, r[k], ff_fnma(al6, w1, a[k]));
-                ff_fma_acc(c.a[k], q, r[k]);
-                ff_fma_acc(c.j[k], q, w1);
-                ff_fma_acc(c.s[k], q, w2);
-            }
+        for (int k = 0; k < 3; ++k) {
+            const ff2 w1 = ff_fnma_lazy(al3, r[k], v[k]);
+            ff_fma_acc_lazy(c.a[k], q, r[k]);
+            ff_fma_acc_lazy(c.j[k], q, w1);
         }
     }
     // End of a j-tile: renormalise the lazily kept sums.
@@ -289,47 +313,11 @@ struct Prec<NB_EX> {
         }
         c.p = ff_renorm(c.p.hi, c.p.lo);
     }
-    static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self, double,
-                                                     float, Acc &c, ff eps2) {
-        const float4 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
-        ff r[3], v[3];
-        r[0] = ff_sub(ff{q0.x, q1.x}, i.x[0]);
-        r[1] = ff_sub(ff{q0.y, q1.y}, i.x[1]);
-        r[2] = ff_sub(ff{q0.z, q1.z}, i.x[2]);
-        v[0] = ff_sub(ff{q2.x, q3.x}, i.v[0]);
-        v[1] = ff_sub(ff{q2.y, q3.y}, i.v[1]);
-        v[2] = ff_sub(ff{q2.z, q3.z}, i.v[2]);
-        ff r2 = NB_EX_LAZY ? ff_dot3_add(r, r, eps2) : ff_add(ff_dot3(r, r), eps2);
-        ff m = ff{q0.w, q1.w};
-        if (self) {
-            r2 = ff{1.f, 0.f};
-            m = ff{0.f, 0.f};
-        }
-        const ff y = rsqrt_ff(r2);
-        const ff y2 = NB_EX_LAZY ? ff_sqr_lazy(y) : ff_sqr(y);
-        const ff my = NB_EX_LAZY ? ff_mul_lazy(m, y) : ff_mul(m, y);
-        const ff q = NB_EX_LAZY ? ff_mul_lazy(my, y2) : ff_mul(my, y2);
-        const ff al3 = NB_EX_LAZY ? ff_mul_f_lazy(ff_mul_lazy(ff_dot3(r, v), y2), 3.0f)
-                                  : ff_mul_f(ff_mul(ff_dot3(r, v), y2), 3.0f);
-        if constexpr (NB_EX_LAZY) {
-            ff_add_lazy(c.p, my);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const ff w1 = ff_fnma_lazy(al3, r[k], v[k]);
-                ff_fma_acc_lazy(c.a[k], q, r[k]);
-                ff_fma_acc_lazy(c.j[k], q, w1);
-            }
-        } else {
-            c.p = ff_add(c.p, my);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const ff w1 = ff_fnma(al3, r[k], v[k]);
-                ff_fma_acc(c.a[k], q, r[k]);
-                ff_fma_acc(c.j[k], q, w1);
-            }
-        }
+    // both lanes' float-float sums as one double (each hi + lo is exact in
+    // FP64; one rounding joins the lanes)
+    static __device__ __forceinline__ double to_d(ff2 a) {
+        return ((double)a.hi.x + (double)a.lo.x) + ((double)a.hi.y + (double)a.lo.y);
     }
-    static __device__ __forceinline__ double to_d(ff a) { return (double)a.hi + (double)a.lo; }
     static __device__ __forceinline__ void finish(const Acc &c, const double *, int, double o[10]) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -342,106 +330,136 @@ struct Prec<NB_EX> {
 };
 
 // ===================================================================== FP32
+// Two j per thread and step: the pair record (J32P) gives both particles'
+// values as two-lane operands, and every add, multiply and FMA of the pair
+// terms is one packed f32x2 instruction (per lane the same IEEE operations
+// as the scalar form).  Lane l of every packed value belongs to particle
+// 2 k + l of the tile.
 template <>
 struct Prec<NB_FP32> {
-    using J = J32;
-    struct I {
-        float xh[3], xl[3], vh[3], vl[3], a[3];
+    using J = J32P;
+    static constexpr int kPerRec = 2;  // particles per record
+    struct I {  // the i-particle's values, both lanes equal
+        float2 xh[3], xl[3], vh[3], vl[3], a[3];
     };
-    // Two FP32 levels: per-tile sums (64 pairs) are added into chunk sums,
-    // which are promoted to FP64 every kFp32FlushTiles tiles.
+    // Two FP32 levels: per-tile sums (64 pairs, two lanes) are added into
+    // chunk sums, which are promoted to FP64 every kFp32FlushTiles tiles.
     struct Acc {
-        float a[3], j[3], s[3], p;
+        float2 a[3], j[3], s[3], p;
         float ca[3], cj[3], cs[3], cp;
     };
     static __device__ __forceinline__ I load_i(const J *jarr, int64_t k) {
-        const J e = jarr[k];
+        const float *f = reinterpret_cast<const float *>(jarr + (k >> 1)) + (k & 1);
         I r;
-        r.xh[0] = e.q[0].x; r.xh[1] = e.q[0].y; r.xh[2] = e.q[0].z;
-        r.xl[0] = e.q[1].x; r.xl[1] = e.q[1].y; r.xl[2] = e.q[1].z;
-        r.vh[0] = e.q[2].x; r.vh[1] = e.q[2].y; r.vh[2] = e.q[2].z;
-        r.vl[0] = e.q[3].x; r.vl[1] = e.q[3].y; r.vl[2] = e.q[3].z;
-        r.a[0] = e.q[1].w; r.a[1] = e.q[2].w; r.a[2] = e.q[3].w;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            r.xh[q] = f2s(f[2 * q]);
+            r.xl[q] = f2s(f[2 * (4 + q)]);
+            r.vh[q] = f2s(f[2 * (8 + q)]);
+            r.vl[q] = f2s(f[2 * (12 + q)]);
+            r.a[q] = f2s(f[2 * (7 + 4 * q)]);
+        }
         return r;
     }
     static __device__ __forceinline__ void zero(Acc &c) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) c.a[k] = c.j[k] = c.s[k] = c.ca[k] = c.cj[k] = c.cs[k] = 0.f;
-        c.p = c.cp = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            c.a[k] = c.j[k] = c.s[k] = make_float2(0.f, 0.f);
+            c.ca[k] = c.cj[k] = c.cs[k] = 0.f;
+        }
+        c.p = make_float2(0.f, 0.f);
+        c.cp = 0.f;
     }
-    static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self, double,
-                                                    float eps2, Acc &c) {
+    // relative coordinates from the hi/lo split: (hi_j - hi_i) + (lo_j - lo_i)
+    static __device__ __forceinline__ void rel(const I &i, const J &jj, float2 r[3], float2 v[3]) {
         const float4 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
-        // relative coordinates from the hi/lo split: (hi_j - hi_i) + (lo_j - lo_i)
-        const float rx = (q0.x - i.xh[0]) + (q1.x - i.xl[0]);
-        const float ry = (q0.y - i.xh[1]) + (q1.y - i.xl[1]);
-        const float rz = (q0.z - i.xh[2]) + (q1.z - i.xl[2]);
-        const float vx = (q2.x - i.vh[0]) + (q3.x - i.vl[0]);
-        const float vy = (q2.y - i.vh[1]) + (q3.y - i.vl[1]);
-        const float vz = (q2.z - i.vh[2]) + (q3.z - i.vl[2]);
-        const float ax = q1.w - i.a[0], ay = q2.w - i.a[1], az = q3.w - i.a[2];
-        float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
-        float m = q0.w;
-        r2 = self ? 1.f : r2;
-        m = self ? 0.f : m;
-        float y;
-        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
-        const float hr2 = 0.5f * r2;             // one Newton step on the SFU value
-        y = y * fmaf(-hr2 * y, y, 1.5f);
-        const float y2 = y * y;
-        const float my = m * y;
-        const float q = my * y2;
-        c.p += my;
-        const float rv = fmaf(rx, vx, fmaf(ry, vy, rz * vz));
-        const float w = fmaf(vx, vx, fmaf(vy, vy, fmaf(vz, vz, fmaf(rx, ax, fmaf(ry, ay, rz * az)))));
-        const float al = rv * y2;
-        const float ze = w * y2;
-        const float al3 = 3.f * al;
-        const float be3 = 3.f * fmaf(al, al, ze);
-        const float al6 = al3 + al3;
-        const float w1x = fmaf(-al3, rx, vx), w1y = fmaf(-al3, ry, vy), w1z = fmaf(-al3, rz, vz);
-        const float w2x = fmaf(-be3, rx, fmaf(-al6, w1x, ax));
-        const float w2y = fmaf(-be3, ry, fmaf(-al6, w1y, ay));
-        const float w2z = fmaf(-be3, rz, fmaf(-al6, w1z, az));
-        c.a[0] = fmaf(q, rx, c.a[0]); c.a[1] = fmaf(q, ry, c.a[1]); c.a[2] = fmaf(q, rz, c.a[2]);
-        c.j[0] = fmaf(q, w1x, c.j[0]); c.j[1] = fmaf(q, w1y, c.j[1]); c.j[2] = fmaf(q, w1z, c.j[2]);
-        c.s[0] = fmaf(q, w2x, c.s[0]); c.s[1] = fmaf(q, w2y, c.s[1]); c.s[2] = fmaf(q, w2z, c.s[2]);
+        const float4 q4 = jj.q[4], q5 = jj.q[5], q6 = jj.q[6], q7 = jj.q[7];
+        r[0] = add2(sub2(lo2(q0), i.xh[0]), sub2(lo2(q2), i.xl[0]));
+        r[1] = add2(sub2(hi2(q0), i.xh[1]), sub2(hi2(q2), i.xl[1]));
+        r[2] = add2(sub2(lo2(q1), i.xh[2]), sub2(lo2(q3), i.xl[2]));
+        v[0] = add2(sub2(lo2(q4), i.vh[0]), sub2(lo2(q6), i.vl[0]));
+        v[1] = add2(sub2(hi2(q4), i.vh[1]), sub2(hi2(q6), i.vl[1]));
+        v[2] = add2(sub2(lo2(q5), i.vh[2]), sub2(lo2(q7), i.vl[2]));
     }
-    static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self, double,
-                                                     float eps2, Acc &c) {
-        const float4 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
-        const float rx = (q0.x - i.xh[0]) + (q1.x - i.xl[0]);
-        const float ry = (q0.y - i.xh[1]) + (q1.y - i.xl[1]);
-        const float rz = (q0.z - i.xh[2]) + (q1.z - i.xl[2]);
-        const float vx = (q2.x - i.vh[0]) + (q3.x - i.vl[0]);
-        const float vy = (q2.y - i.vh[1]) + (q3.y - i.vl[1]);
-        const float vz = (q2.z - i.vh[2]) + (q3.z - i.vl[2]);
-        float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
-        float m = q0.w;
-        r2 = self ? 1.f : r2;
-        m = self ? 0.f : m;
-        float y;
-        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
-        const float hr2 = 0.5f * r2;
-        y = y * fmaf(-hr2 * y, y, 1.5f);
-        const float y2 = y * y;
-        const float my = m * y;
-        const float q = my * y2;
-        c.p += my;
-        const float al3 = 3.f * (fmaf(rx, vx, fmaf(ry, vy, rz * vz)) * y2);
-        const float w1x = fmaf(-al3, rx, vx), w1y = fmaf(-al3, ry, vy), w1z = fmaf(-al3, rz, vz);
-        c.a[0] = fmaf(q, rx, c.a[0]); c.a[1] = fmaf(q, ry, c.a[1]); c.a[2] = fmaf(q, rz, c.a[2]);
-        c.j[0] = fmaf(q, w1x, c.j[0]); c.j[1] = fmaf(q, w1y, c.j[1]); c.j[2] = fmaf(q, w1z, c.j[2]);
+    // 1/sqrt(r2) per lane: SFU value and one Newton step y (3/2 - r2 y^2 / 2)
+    static __device__ __forceinline__ float2 rsqrt2(float2 r2) {
+        float2 y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y.x) : "f"(r2.x));
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y.y) : "f"(r2.y));
+        const float2 t = mul2(mul2(f2s(-0.5f), r2), y);
+        return mul2(y, fma2(t, y, f2s(1.5f)));
     }
-    // End of a tile: add the tile sums into the chunk sums.
+    static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self0, bool self1,
+                                                    float2 eps2, Acc &c) {
+        float2 r[3], v[3];
+        rel(i, jj, r, v);
+        const float2 ax = sub2(hi2(jj.q[3]), i.a[0]);
+        const float2 ay = sub2(hi2(jj.q[5]), i.a[1]);
+        const float2 az = sub2(hi2(jj.q[7]), i.a[2]);
+        float2 r2 = fma2(r[0], r[0], fma2(r[1], r[1], fma2(r[2], r[2], eps2)));
+        float2 m = hi2(jj.q[1]);
+        r2.x = self0 ? 1.f : r2.x;  // selects, not arithmetic
+        r2.y = self1 ? 1.f : r2.y;
+        m.x = self0 ? 0.f : m.x;
+        m.y = self1 ? 0.f : m.y;
+        const float2 y = rsqrt2(r2);
+        const float2 y2 = mul2(y, y);
+        const float2 my = mul2(m, y);
+        const float2 q = mul2(my, y2);
+        c.p = add2(c.p, my);
+        const float2 rv = fma2(r[0], v[0], fma2(r[1], v[1], mul2(r[2], v[2])));
+        const float2 w = fma2(v[0], v[0], fma2(v[1], v[1], fma2(v[2], v[2],
+                         fma2(r[0], ax, fma2(r[1], ay, mul2(r[2], az))))));
+        const float2 al = mul2(rv, y2);
+        const float2 ze = mul2(w, y2);
+        const float2 nal3 = mul2(f2s(-3.f), al);              // -3 alpha
+        const float2 nbe3 = mul2(f2s(-3.f), fma2(al, al, ze)); // -3 beta
+        const float2 nal6 = add2(nal3, nal3);
+        const float2 aa[3] = {ax, ay, az};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float2 w1 = fma2(nal3, r[k], v[k]);
+            const float2 w2 = fma2(nbe3, r[k], fma2(nal6, w1, aa[k]));
+            c.a[k] = fma2(q, r[k], c.a[k]);
+            c.j[k] = fma2(q, w1, c.j[k]);
+            c.s[k] = fma2(q, w2, c.s[k]);
+        }
+    }
+    static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self0, bool self1,
+                                                     float2 eps2, Acc &c) {
+        float2 r[3], v[3];
+        rel(i, jj, r, v);
+        float2 r2 = fma2(r[0], r[0], fma2(r[1], r[1], fma2(r[2], r[2], eps2)));
+        float2 m = hi2(jj.q[1]);
+        r2.x = self0 ? 1.f : r2.x;
+        r2.y = self1 ? 1.f : r2.y;
+        m.x = self0 ? 0.f : m.x;
+        m.y = self1 ? 0.f : m.y;
+        const float2 y = rsqrt2(r2);
+        const float2 y2 = mul2(y, y);
+        const float2 my = mul2(m, y);
+        const float2 q = mul2(my, y2);
+        c.p = add2(c.p, my);
+        const float2 nal3 =
+            mul2(f2s(-3.f), mul2(fma2(r[0], v[0], fma2(r[1], v[1], mul2(r[2], v[2]))), y2));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float2 w1 = fma2(nal3, r[k], v[k]);
+            c.a[k] = fma2(q, r[k], c.a[k]);
+            c.j[k] = fma2(q, w1, c.j[k]);
+        }
+    }
+    // End of a tile: add both lanes of the tile sums into the chunk sums.
     static __device__ __forceinline__ void tile_done(Acc &c) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            c.ca[k] += c.a[k]; c.cj[k] += c.j[k]; c.cs[k] += c.s[k];
-            c.a[k] = c.j[k] = c.s[k] = 0.f;
+            c.ca[k] += c.a[k].x + c.a[k].y;
+            c.cj[k] += c.j[k].x + c.j[k].y;
+            c.cs[k] += c.s[k].x + c.s[k].y;
+            c.a[k] = c.j[k] = c.s[k] = make_float2(0.f, 0.f);
         }
-        c.cp += c.p;
-        c.p = 0.f;
+        c.cp += c.p.x + c.p.y;
+        c.p = make_float2(0.f, 0.f);
     }
     // Promote the FP32 chunk sums into the FP64 totals and restart them.
     // t64: the ten FP64 totals, element q at t64[q * st]
@@ -478,6 +496,15 @@ struct EvalCfg<NB_EX> {
     static constexpr int min_blocks = NB_EX_MIN_BLOCKS;
     static constexpr bool t64_smem = false;
 };
+// Resident CTAs per SM the compiler must allow for one kernel.  The packed EX
+// pair terms of the 4th-order modes measured faster at 3 CTAs per SM (140
+// registers: 1.16e11 against 1.10e11 pairs/s at 4 CTAs, N = 65536); the
+// 6th-order ones are as fast at 4 (128 registers) as at 3 (166).
+template <int P, int MODE>
+constexpr int eval_min_blocks() {
+    if constexpr (P == NB_EX && is_order4_mode(MODE)) return NB_EX4_MIN_BLOCKS;
+    return EvalCfg<P>::min_blocks;
+}
 template <>
 struct EvalCfg<NB_FP32> {
     static constexpr int stages = NB_FP32_STAGES;
@@ -495,7 +522,7 @@ struct PieceRec {
 
 template <int P>
 struct SmemLayout {
-    typename Prec<P>::J tile[EvalCfg<P>::stages][kTJ];
+    typename Prec<P>::J tile[EvalCfg<P>::stages][kTJ / Prec<P>::kPerRec];
     double red[10 * kTPB];  // cross-split reduction: group sums, then totals
     double t64[EvalCfg<P>::t64_smem ? 10 * kTPB : 1];  // FP32 totals, [q][thread]
     uint64_t bar[EvalCfg<P>::stages];
@@ -546,10 +573,11 @@ __device__ __forceinline__ int64_t sk_units(const Dev &d, const EvalLaunch &L) {
 }
 
 template <int P, int MODE>
-__global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev d, const EvalLaunch L) {
+__global__ void __launch_bounds__(kTPB, (eval_min_blocks<P, MODE>())) k_eval(const Dev d, const EvalLaunch L) {
     using T = Prec<P>;
     constexpr int kSt = EvalCfg<P>::stages;
     using J = typename T::J;
+    constexpr int kRecs = kTJ / T::kPerRec;  // records per j-tile
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemLayout<P> &S = *reinterpret_cast<SmemLayout<P> *>(smem_raw);
     PieceRec &R = S.pc;
@@ -628,7 +656,7 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
         const int ilane = tid / gl;
         const int jsub = tid % gl;
         const bool valid = R.tile * (kTPB / gl) + ilane < R.A;
-        const J *jc = reinterpret_cast<const J *>(d.jarr) + d.jofs[c];
+        const J *jc = reinterpret_cast<const J *>(d.jarr) + d.jofs[c] / T::kPerRec;
         // this thread's i: global index, bounds-checked against its cluster
         auto i_of = [&](int il, bool &bad) -> int64_t {
             const int64_t off = R.off;
@@ -656,17 +684,18 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
         for (int q = 0; q < 10; ++q) t64[q * t64st] = 0.0;
         const double eps2 = d.eps2;
         const float eps2f = (float)eps2;
-        ff eps2ff;
-        eps2ff.hi = (float)eps2;
-        eps2ff.lo = (float)(eps2 - (double)eps2ff.hi);
+        const float2 eps2f2 = make_float2(eps2f, eps2f);
+        ff2 eps2ff2;
+        eps2ff2.hi = f2s((float)eps2);
+        eps2ff2.lo = f2s((float)(eps2 - (double)(float)eps2));
 
         const bool warp_active = __any_sync(0xffffffffu, valid);
 
         // prologue: fill the ring
         if (tid == 0) {
             for (int s = 0; s < kSt && tb + s < te; ++s) {
-                mbar_expect_tx(&S.bar[s], kTJ * sizeof(J));
-                tma_load_1d(&S.tile[s][0], jc + (tb + s) * kTJ, kTJ * sizeof(J), &S.bar[s]);
+                mbar_expect_tx(&S.bar[s], kRecs * sizeof(J));
+                tma_load_1d(&S.tile[s][0], jc + (tb + s) * kRecs, kRecs * sizeof(J), &S.bar[s]);
                 pending |= 1u << s;
             }
         }
@@ -681,14 +710,27 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
                 if constexpr (MODE == kModePot) {
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact_pot(me, tl[k], jbase + k == ji, eps2, acc);
+                } else if constexpr (P == NB_FP32 && uses_order4_terms(MODE)) {
+                    // record k holds particles 2k and 2k + 1 of the tile
+#pragma unroll kEvalUnroll
+                    for (int k = jsub; k < kRecs; k += gl)
+                        T::interact4(me, tl[k], jbase + 2 * k == ji, jbase + 2 * k + 1 == ji,
+                                     eps2f2, acc);
+                } else if constexpr (P == NB_FP32) {
+#pragma unroll kEvalUnroll
+                    for (int k = jsub; k < kRecs; k += gl)
+                        T::interact(me, tl[k], jbase + 2 * k == ji, jbase + 2 * k + 1 == ji,
+                                    eps2f2, acc);
                 } else if constexpr (P == NB_EX && uses_order4_terms(MODE)) {
 #pragma unroll 1
-                    for (int k = jsub; k < kTJ; k += gl)
-                        T::interact4(me, tl[k], jbase + k == ji, eps2, eps2f, acc, eps2ff);
+                    for (int k = jsub; k < kRecs; k += gl)
+                        T::interact4(me, tl[k], jbase + 2 * k == ji, jbase + 2 * k + 1 == ji,
+                                     eps2ff2, acc);
                 } else if constexpr (P == NB_EX) {
 #pragma unroll 1
-                    for (int k = jsub; k < kTJ; k += gl)
-                        T::interact(me, tl[k], jbase + k == ji, eps2, eps2f, acc, eps2ff);
+                    for (int k = jsub; k < kRecs; k += gl)
+                        T::interact(me, tl[k], jbase + 2 * k == ji, jbase + 2 * k + 1 == ji,
+                                    eps2ff2, acc);
                 } else if constexpr (uses_order4_terms(MODE)) {
 #pragma unroll kEvalUnroll
                     for (int k = jsub; k < kTJ; k += gl)
@@ -701,7 +743,7 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
                 if constexpr (P == NB_FP32) {
                     if ((tt - tb + 1) % kFp32FlushTiles == 0) T::flush(acc, t64, t64st);
                     else T::tile_done(acc);
-                } else if constexpr (P == NB_EX && NB_EX_LAZY && MODE != kModePot) {
+                } else if constexpr (P == NB_EX && MODE != kModePot) {
                     T::tile_done(acc);
                 } else if constexpr (P == NB_FP64 && NB_FP64_POT_FF && MODE != kModePot) {
                     T::tile_done(acc);
@@ -713,8 +755,8 @@ __global__ void __launch_bounds__(kTPB, EvalCfg<P>::min_blocks) k_eval(const Dev
             if (tid == 0) {
                 pending &= ~(1u << s);
                 if (tt + kSt < te) {
-                    mbar_expect_tx(&S.bar[s], kTJ * sizeof(J));
-                    tma_load_1d(&S.tile[s][0], jc + (tt + kSt) * kTJ, kTJ * sizeof(J), &S.bar[s]);
+                    mbar_expect_tx(&S.bar[s], kRecs * sizeof(J));
+                    tma_load_1d(&S.tile[s][0], jc + (tt + kSt) * kRecs, kRecs * sizeof(J), &S.bar[s]);
                     pending |= 1u << s;
                 }
             }

@@ -52,6 +52,9 @@ constexpr int kTJ = 64;        // j-particles per shared-memory tile
 #ifndef NB_EX_MIN_BLOCKS
 #define NB_EX_MIN_BLOCKS NB_EVAL_MIN_BLOCKS
 #endif
+#ifndef NB_EX4_MIN_BLOCKS
+#define NB_EX4_MIN_BLOCKS 3
+#endif
 #ifndef NB_FP32_T64_SMEM
 #define NB_FP32_T64_SMEM 1
 #endif
@@ -101,15 +104,43 @@ __host__ __device__ inline void j64_set_mass_split(J64 &w, double m) {
     (void)m;
 #endif
 }
-// EX: hi/lo single pairs: (xh,yh,zh,mh) (xl,yl,zl,ml) (vxh,vyh,vzh,axh)
-//     (vxl,vyl,vzl,axl) (ayh,azh,ayl,azl)
-struct alignas(16) JEX {
+// EX: 80 bytes per particle (hi/lo single pairs), stored as records of two
+// particles whose values interleave like the FP32 records below: value f of
+// lane l of record r is float r * 40 + 2 f + l, f in the order
+//   xh, yh, zh, mh, xl, yl, zl, ml, vxh, vyh, vzh, axh, vxl, vyl, vzl, axl,
+//   ayh, azh, ayl, azl
+// so q[k] of a record holds (value 2k of lanes 0, 1; value 2k + 1 of lanes 0, 1).
+struct alignas(16) JEX {  // one particle's share of the array (sizing only)
     float4 q[5];
 };
-// FP32: (xh,yh,zh,m) (xl,yl,zl,ax) (vxh,vyh,vzh,ay) (vxl,vyl,vzl,az)
-struct alignas(16) J32 {
+struct alignas(16) JEXP {  // a record of two particles
+    float4 q[10];
+};
+constexpr int kJEXVals = 20;
+// FP32: 64 bytes per particle, stored as records of two particles whose
+// values interleave, so that one 16-byte shared-memory load gives two
+// two-lane operands of the packed FP32 arithmetic.  Value f of lane l (the
+// particle's index parity) of record r is float r * 32 + 2 f + l, f in the
+// order xh, yh, zh, m, xl, yl, zl, ax, vxh, vyh, vzh, ay, vxl, vyl, vzl, az:
+//   q[0] = (xh0, xh1, yh0, yh1)  q[1] = (zh0, zh1, m0, m1)
+//   q[2] = (xl0, xl1, yl0, yl1)  q[3] = (zl0, zl1, ax0, ax1)
+//   q[4] = (vxh0, vxh1, vyh0, vyh1)  q[5] = (vzh0, vzh1, ay0, ay1)
+//   q[6] = (vxl0, vxl1, vyl0, vyl1)  q[7] = (vzl0, vzl1, az0, az1)
+struct alignas(16) J32 {  // one particle's share of the array (sizing only)
     float4 q[4];
 };
+struct alignas(16) J32P {  // a record of two particles
+    float4 q[8];
+};
+constexpr int kJ32Vals = 16;
+// Write particle jx's NV values (the orders above) into a two-particle
+// record array (FP32: NV = 16, EX: NV = 20).
+template <int NV>
+__device__ __forceinline__ void jpair_store(void *jarr, int64_t jx, const float v[NV]) {
+    float *p = reinterpret_cast<float *>(jarr) + (jx >> 1) * (2 * NV) + (jx & 1);
+#pragma unroll
+    for (int f = 0; f < NV; ++f) p[2 * f] = v[f];
+}
 
 // ------------------------------------------------------------ planning data
 struct ClusterPlan {
@@ -336,99 +367,159 @@ __device__ __forceinline__ double twice_int(double x) {
     return __hiloint2double(ok ? hi + 0x00100000 : hi, __double2loint(x));
 }
 
+// --------------------------------------------- packed two-lane FP32 (f32x2)
+// sm_100 and later execute FP32 add / multiply / FMA on a pair of floats in
+// one instruction (PTX add/sub/mul/fma.rn.f32x2): the same per-lane IEEE
+// round-to-nearest results as the scalar instructions, half the issue slots.
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 ta, tb, tr;\n\tmov.b64 ta, {%2, %3};\n\tmov.b64 tb, {%4, %5};\n\t"
+        "sub.rn.f32x2 tr, ta, tb;\n\tmov.b64 {%0, %1}, tr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 lo2(float4 q) { return make_float2(q.x, q.y); }
+__device__ __forceinline__ float2 hi2(float4 q) { return make_float2(q.z, q.w); }
+
 // ------------------------------------------------------- float-float (EX)
 // A value is hi + lo with |lo| <= ulp(hi)/2 (Dekker 1971; Knuth TAOCP 2;
 // Hida, Li & Bailey 2001 for the double-double algorithms, here on floats).
-struct ff {
-    float hi, lo;
+// Every primitive is written once for a lane type T: float (one value) or
+// float2 (two independent values, one per lane, each with the IEEE results
+// of the float form, evaluated by the packed f32x2 instructions).
+template <class T>
+struct ffT {
+    T hi, lo;
 };
+using ff = ffT<float>;
+using ff2 = ffT<float2>;
 
+__device__ __forceinline__ float o_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float o_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float o_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float o_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float o_neg(float a) { return -a; }
+__device__ __forceinline__ float o_cst(float, float c) { return c; }
+__device__ __forceinline__ float2 o_add(float2 a, float2 b) { return add2(a, b); }
+__device__ __forceinline__ float2 o_sub(float2 a, float2 b) { return sub2(a, b); }
+__device__ __forceinline__ float2 o_mul(float2 a, float2 b) { return mul2(a, b); }
+__device__ __forceinline__ float2 o_fma(float2 a, float2 b, float2 c) { return fma2(a, b, c); }
+__device__ __forceinline__ float2 o_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 o_cst(float2, float c) { return f2s(c); }
 
 // exact: s + e = a + b (Knuth TwoSum)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+template <class T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+    s = o_add(a, b);
+    const T bb = o_sub(s, a);
+    e = o_add(o_sub(a, o_sub(s, bb)), o_sub(b, bb));
+}
+// exact: s + e = a - b (TwoSum of a and -b, the negation folded in)
+template <class T>
+__device__ __forceinline__ void two_diff(T a, T b, T &s, T &e) {
+    s = o_sub(a, b);
+    const T bb = o_sub(s, a);
+    e = o_sub(o_sub(a, o_sub(s, bb)), o_add(b, bb));
 }
 // exact when |a| >= |b| (Dekker FastTwoSum)
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
+template <class T>
+__device__ __forceinline__ void fast_two_sum(T a, T b, T &s, T &e) {
+    s = o_add(a, b);
+    e = o_sub(b, o_sub(s, a));
 }
-__device__ __forceinline__ ff ff_renorm(float s, float e) {
-    ff r;
+template <class T>
+__device__ __forceinline__ ffT<T> ff_renorm(T s, T e) {
+    ffT<T> r;
     fast_two_sum(s, e, r.hi, r.lo);
     return r;
 }
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    float s, e;
+template <class T>
+__device__ __forceinline__ ffT<T> ff_add(ffT<T> a, ffT<T> b) {
+    T s, e;
     two_sum(a.hi, b.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    e = o_add(e, o_add(a.lo, b.lo));
     return ff_renorm(s, e);
 }
-__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
-__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+template <class T>
+__device__ __forceinline__ ffT<T> ff_neg(ffT<T> a) { return ffT<T>{o_neg(a.hi), o_neg(a.lo)}; }
+// a - b, normalised
+template <class T>
+__device__ __forceinline__ ffT<T> ff_sub(ffT<T> a, ffT<T> b) {
+    T s, e;
+    two_diff(a.hi, b.hi, s, e);
+    e = o_add(e, o_sub(a.lo, b.lo));
+    return ff_renorm(s, e);
+}
 // product, error terms folded with FMA (Dekker TwoProduct via FMA)
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
+template <class T>
+__device__ __forceinline__ ffT<T> ff_mul(ffT<T> a, ffT<T> b) {
+    const T p = o_mul(a.hi, b.hi);
+    T e = o_fma(a.hi, b.hi, o_neg(p));
+    e = o_fma(a.hi, b.lo, e);
+    e = o_fma(a.lo, b.hi, e);
     return ff_renorm(p, e);
 }
-__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
-    const float p = __fmul_rn(a.hi, b);
-    float e = __fmaf_rn(a.hi, b, -p);
-    e = __fmaf_rn(a.lo, b, e);
+template <class T>
+__device__ __forceinline__ ffT<T> ff_mul_f(ffT<T> a, T b) {
+    const T p = o_mul(a.hi, b);
+    T e = o_fma(a.hi, b, o_neg(p));
+    e = o_fma(a.lo, b, e);
     return ff_renorm(p, e);
 }
-__device__ __forceinline__ ff ff_sqr(ff a) {
-    const float p = __fmul_rn(a.hi, a.hi);
-    float e = __fmaf_rn(a.hi, a.hi, -p);
-    e = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, e);
+template <class T>
+__device__ __forceinline__ ffT<T> ff_sqr(ffT<T> a) {
+    const T p = o_mul(a.hi, a.hi);
+    T e = o_fma(a.hi, a.hi, o_neg(p));
+    e = o_fma(o_add(a.hi, a.hi), a.lo, e);
     return ff_renorm(p, e);
 }
 // acc += a * b, product and sum kept exact to float-float accuracy
-__device__ __forceinline__ void ff_fma_acc(ff &acc, ff a, ff b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float pe = __fmaf_rn(a.hi, b.hi, -p);
-    pe = __fmaf_rn(a.hi, b.lo, pe);
-    pe = __fmaf_rn(a.lo, b.hi, pe);
-    float s, e;
+template <class T>
+__device__ __forceinline__ void ff_fma_acc(ffT<T> &acc, ffT<T> a, ffT<T> b) {
+    const T p = o_mul(a.hi, b.hi);
+    T pe = o_fma(a.hi, b.hi, o_neg(p));
+    pe = o_fma(a.hi, b.lo, pe);
+    pe = o_fma(a.lo, b.hi, pe);
+    T s, e;
     two_sum(acc.hi, p, s, e);
-    e = __fadd_rn(e, __fadd_rn(acc.lo, pe));
+    e = o_add(e, o_add(acc.lo, pe));
     acc = ff_renorm(s, e);
 }
 // a - b*c: the product's error terms folded by FMA, one renormalisation
-__device__ __forceinline__ ff ff_fnma(ff b, ff c, ff a) {
-    const float p = __fmul_rn(b.hi, c.hi);
-    float pe = __fmaf_rn(b.hi, c.hi, -p);
-    pe = __fmaf_rn(b.hi, c.lo, pe);
-    pe = __fmaf_rn(b.lo, c.hi, pe);
-    float s, e;
-    two_sum(a.hi, -p, s, e);
-    e = __fadd_rn(e, __fsub_rn(a.lo, pe));
+template <class T>
+__device__ __forceinline__ ffT<T> ff_fnma(ffT<T> b, ffT<T> c, ffT<T> a) {
+    const T p = o_mul(b.hi, c.hi);
+    T pe = o_fma(b.hi, c.hi, o_neg(p));
+    pe = o_fma(b.hi, c.lo, pe);
+    pe = o_fma(b.lo, c.hi, pe);
+    T s, e;
+    two_diff(a.hi, p, s, e);
+    e = o_add(e, o_sub(a.lo, pe));
     return ff_renorm(s, e);
 }
 // dot products: high parts summed with exact TwoSum, all second-order terms
-// gathered in one float, one renormalisation at the end.
-__device__ __forceinline__ ff ff_dot3(const ff a[3], const ff b[3]) {
-    float p0 = __fmul_rn(a[0].hi, b[0].hi), p1 = __fmul_rn(a[1].hi, b[1].hi),
-          p2 = __fmul_rn(a[2].hi, b[2].hi);
-    float lo = __fmaf_rn(a[0].hi, b[0].hi, -p0);
-    lo = __fmaf_rn(a[1].hi, b[1].hi, -p1) + lo;
-    lo = __fmaf_rn(a[2].hi, b[2].hi, -p2) + lo;
-    lo = __fmaf_rn(a[0].hi, b[0].lo, lo);
-    lo = __fmaf_rn(a[0].lo, b[0].hi, lo);
-    lo = __fmaf_rn(a[1].hi, b[1].lo, lo);
-    lo = __fmaf_rn(a[1].lo, b[1].hi, lo);
-    lo = __fmaf_rn(a[2].hi, b[2].lo, lo);
-    lo = __fmaf_rn(a[2].lo, b[2].hi, lo);
-    float s, e;
+// gathered in one value, one renormalisation at the end.
+template <class T>
+__device__ __forceinline__ ffT<T> ff_dot3(const ffT<T> a[3], const ffT<T> b[3]) {
+    T p0 = o_mul(a[0].hi, b[0].hi), p1 = o_mul(a[1].hi, b[1].hi), p2 = o_mul(a[2].hi, b[2].hi);
+    T lo = o_fma(a[0].hi, b[0].hi, o_neg(p0));
+    lo = o_add(o_fma(a[1].hi, b[1].hi, o_neg(p1)), lo);
+    lo = o_add(o_fma(a[2].hi, b[2].hi, o_neg(p2)), lo);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo = o_fma(a[k].hi, b[k].lo, lo);
+        lo = o_fma(a[k].lo, b[k].hi, lo);
+    }
+    T s, e;
     two_sum(p0, p1, s, e);
-    lo = __fadd_rn(lo, e);
+    lo = o_add(lo, e);
     two_sum(s, p2, s, e);
-    lo = __fadd_rn(lo, e);
+    lo = o_add(lo, e);
     return ff_renorm(s, lo);
 }
 
@@ -436,71 +527,86 @@ __device__ __forceinline__ ff ff_dot3(const ff a[3], const ff b[3]) {
 // gathers every error term, and renormalisation is left to the caller (once
 // per j-tile for accumulators).  |lo| may reach a few ulps of |hi|; every
 // consumer below folds lo into first-order terms only.
-__device__ __forceinline__ void ff_fma_acc_lazy(ff &acc, ff a, ff b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float pe = __fmaf_rn(a.hi, b.hi, -p);
-    pe = __fmaf_rn(a.hi, b.lo, pe);
-    pe = __fmaf_rn(a.lo, b.hi, pe);
-    float s, e;
+template <class T>
+__device__ __forceinline__ void ff_fma_acc_lazy(ffT<T> &acc, ffT<T> a, ffT<T> b) {
+    const T p = o_mul(a.hi, b.hi);
+    T pe = o_fma(a.hi, b.hi, o_neg(p));
+    pe = o_fma(a.hi, b.lo, pe);
+    pe = o_fma(a.lo, b.hi, pe);
+    T s, e;
     two_sum(acc.hi, p, s, e);
     acc.hi = s;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
+    acc.lo = o_add(acc.lo, o_add(e, pe));
 }
-__device__ __forceinline__ ff ff_mul_lazy(ff a, ff b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    return ff{p, e};
+template <class T>
+__device__ __forceinline__ ffT<T> ff_mul_lazy(ffT<T> a, ffT<T> b) {
+    const T p = o_mul(a.hi, b.hi);
+    T e = o_fma(a.hi, b.hi, o_neg(p));
+    e = o_fma(a.hi, b.lo, e);
+    e = o_fma(a.lo, b.hi, e);
+    return ffT<T>{p, e};
 }
-__device__ __forceinline__ ff ff_mul_f_lazy(ff a, float b) {
-    const float p = __fmul_rn(a.hi, b);
-    float e = __fmaf_rn(a.hi, b, -p);
-    e = __fmaf_rn(a.lo, b, e);
-    return ff{p, e};
+template <class T>
+__device__ __forceinline__ ffT<T> ff_mul_f_lazy(ffT<T> a, T b) {
+    const T p = o_mul(a.hi, b);
+    T e = o_fma(a.hi, b, o_neg(p));
+    e = o_fma(a.lo, b, e);
+    return ffT<T>{p, e};
 }
-__device__ __forceinline__ ff ff_sqr_lazy(ff a) {
-    const float p = __fmul_rn(a.hi, a.hi);
-    float e = __fmaf_rn(a.hi, a.hi, -p);
-    e = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, e);
-    return ff{p, e};
+template <class T>
+__device__ __forceinline__ ffT<T> ff_sqr_lazy(ffT<T> a) {
+    const T p = o_mul(a.hi, a.hi);
+    T e = o_fma(a.hi, a.hi, o_neg(p));
+    e = o_fma(o_add(a.hi, a.hi), a.lo, e);
+    return ffT<T>{p, e};
 }
-__device__ __forceinline__ ff ff_sum_lazy(ff a, ff b) {
-    float s, e;
+template <class T>
+__device__ __forceinline__ ffT<T> ff_sum_lazy(ffT<T> a, ffT<T> b) {
+    T s, e;
     two_sum(a.hi, b.hi, s, e);
-    return ff{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+    return ffT<T>{s, o_add(e, o_add(a.lo, b.lo))};
 }
-__device__ __forceinline__ void ff_add_lazy(ff &acc, ff b) {
-    float s, e;
+template <class T>
+__device__ __forceinline__ void ff_add_lazy(ffT<T> &acc, ffT<T> b) {
+    T s, e;
     two_sum(acc.hi, b.hi, s, e);
     acc.hi = s;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, b.lo));
+    acc.lo = o_add(acc.lo, o_add(e, b.lo));
 }
-__device__ __forceinline__ ff ff_fnma_lazy(ff b, ff c, ff a) {
-    const float p = __fmul_rn(b.hi, c.hi);
-    float pe = __fmaf_rn(b.hi, c.hi, -p);
-    pe = __fmaf_rn(b.hi, c.lo, pe);
-    pe = __fmaf_rn(b.lo, c.hi, pe);
-    float s, e;
-    two_sum(a.hi, -p, s, e);
-    return ff{s, __fadd_rn(e, __fsub_rn(a.lo, pe))};
+template <class T>
+__device__ __forceinline__ ffT<T> ff_fnma_lazy(ffT<T> b, ffT<T> c, ffT<T> a) {
+    const T p = o_mul(b.hi, c.hi);
+    T pe = o_fma(b.hi, c.hi, o_neg(p));
+    pe = o_fma(b.hi, c.lo, pe);
+    pe = o_fma(b.lo, c.hi, pe);
+    T s, e;
+    two_diff(a.hi, p, s, e);
+    return ffT<T>{s, o_add(e, o_sub(a.lo, pe))};
 }
 // 1/sqrt(r2) in float-float: SFU seed y0, residual e = 1 - r2 y0^2 from the
 // exact square of y0 and FMA-exact products, then y0 (1 + e/2 + 3e^2/8).
 // Lazy form: y0 + corr as it is (|corr| ~ 2^-22 |y0|).  Domain: the normal
 // FP32 range of r2.hi.
-__device__ __forceinline__ ff rsqrt_ff(ff r2) {
-    float y0;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.hi));
-    const float p = __fmul_rn(y0, y0);
-    const float pe = __fmaf_rn(y0, y0, -p);
-    const float u = __fmul_rn(r2.hi, p);
-    float ue = __fmaf_rn(r2.hi, p, -u);
-    ue = __fmaf_rn(r2.hi, pe, ue);
-    ue = __fmaf_rn(r2.lo, p, ue);
-    const float e = __fsub_rn(__fsub_rn(1.0f, u), ue);
-    const float corr = __fmul_rn(__fmul_rn(y0, e), __fmaf_rn(e, 0.375f, 0.5f));
-    if constexpr (NB_EX_LAZY) return ff{y0, corr};
+__device__ __forceinline__ float rsqrt_sfu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 rsqrt_sfu(float2 x) {
+    return make_float2(rsqrt_sfu(x.x), rsqrt_sfu(x.y));
+}
+template <class T>
+__device__ __forceinline__ ffT<T> rsqrt_ff(ffT<T> r2) {
+    const T y0 = rsqrt_sfu(r2.hi);
+    const T p = o_mul(y0, y0);
+    const T pe = o_fma(y0, y0, o_neg(p));
+    const T u = o_mul(r2.hi, p);
+    T ue = o_fma(r2.hi, p, o_neg(u));
+    ue = o_fma(r2.hi, pe, ue);
+    ue = o_fma(r2.lo, p, ue);
+    const T e = o_sub(o_sub(o_cst(y0, 1.0f), u), ue);
+    const T corr = o_mul(o_mul(y0, e), o_fma(e, o_cst(y0, 0.375f), o_cst(y0, 0.5f)));
+    if constexpr (NB_EX_LAZY) return ffT<T>{y0, corr};
     else return ff_renorm(y0, corr);
 }
 
@@ -517,107 +623,76 @@ __device__ __forceinline__ ff ff_from_pos_double(double y) {
 }
 
 // a.b, unnormalised (hi + lo with every error term in lo)
-__device__ __forceinline__ ff ff_dot3_lazy(const ff a[3], const ff b[3]) {
-    float p[3], lo;
+template <class T>
+__device__ __forceinline__ ffT<T> ff_dot3_lazy(const ffT<T> a[3], const ffT<T> b[3]) {
+    T p[3], lo;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) p[k] = __fmul_rn(a[k].hi, b[k].hi);
-    lo = __fmaf_rn(a[0].hi, b[0].hi, -p[0]);
+    for (int k = 0; k < 3; ++k) p[k] = o_mul(a[k].hi, b[k].hi);
+    lo = o_fma(a[0].hi, b[0].hi, o_neg(p[0]));
 #pragma unroll
-    for (int k = 1; k < 3; ++k) lo = __fmaf_rn(a[k].hi, b[k].hi, -p[k]) + lo;
+    for (int k = 1; k < 3; ++k) lo = o_add(o_fma(a[k].hi, b[k].hi, o_neg(p[k])), lo);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        lo = __fmaf_rn(a[k].hi, b[k].lo, lo);
-        lo = __fmaf_rn(a[k].lo, b[k].hi, lo);
+        lo = o_fma(a[k].hi, b[k].lo, lo);
+        lo = o_fma(a[k].lo, b[k].hi, lo);
     }
-    float s = p[0], e;
+    T s = p[0], e;
 #pragma unroll
     for (int k = 1; k < 3; ++k) {
         two_sum(s, p[k], s, e);
-        lo = __fadd_rn(lo, e);
+        lo = o_add(lo, e);
     }
-    return ff{s, lo};
+    return ffT<T>{s, lo};
 }
 // a0.b0 + a1.b1, unnormalised
-__device__ __forceinline__ ff ff_dot3x2_lazy(const ff a0[3], const ff b0[3], const ff a1[3],
-                                             const ff b1[3]) {
-    float p[6], lo = 0.f;
+template <class T>
+__device__ __forceinline__ ffT<T> ff_dot3x2_lazy(const ffT<T> a0[3], const ffT<T> b0[3],
+                                                 const ffT<T> a1[3], const ffT<T> b1[3]) {
+    T p[6];
+    T lo = o_cst(a0[0].hi, 0.f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        p[k] = __fmul_rn(a0[k].hi, b0[k].hi);
-        p[3 + k] = __fmul_rn(a1[k].hi, b1[k].hi);
-        lo = __fmaf_rn(a0[k].hi, b0[k].hi, -p[k]) + lo;
-        lo = __fmaf_rn(a1[k].hi, b1[k].hi, -p[3 + k]) + lo;
-        lo = __fmaf_rn(a0[k].hi, b0[k].lo, lo);
-        lo = __fmaf_rn(a0[k].lo, b0[k].hi, lo);
-        lo = __fmaf_rn(a1[k].hi, b1[k].lo, lo);
-        lo = __fmaf_rn(a1[k].lo, b1[k].hi, lo);
+        p[k] = o_mul(a0[k].hi, b0[k].hi);
+        p[3 + k] = o_mul(a1[k].hi, b1[k].hi);
+        lo = o_add(o_fma(a0[k].hi, b0[k].hi, o_neg(p[k])), lo);
+        lo = o_add(o_fma(a1[k].hi, b1[k].hi, o_neg(p[3 + k])), lo);
+        lo = o_fma(a0[k].hi, b0[k].lo, lo);
+        lo = o_fma(a0[k].lo, b0[k].hi, lo);
+        lo = o_fma(a1[k].hi, b1[k].lo, lo);
+        lo = o_fma(a1[k].lo, b1[k].hi, lo);
     }
-    float s = p[0], e;
+    T s = p[0], e;
 #pragma unroll
     for (int k = 1; k < 6; ++k) {
         two_sum(s, p[k], s, e);
-        lo = __fadd_rn(lo, e);
+        lo = o_add(lo, e);
     }
-    return ff{s, lo};
+    return ffT<T>{s, lo};
 }
 // a.b + c, unnormalised
-__device__ __forceinline__ ff ff_dot3_add_lazy(const ff a[3], const ff b[3], ff c) {
-    float p[3], lo = c.lo;
+template <class T>
+__device__ __forceinline__ ffT<T> ff_dot3_add_lazy(const ffT<T> a[3], const ffT<T> b[3], ffT<T> c) {
+    T p[3], lo = c.lo;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        p[k] = __fmul_rn(a[k].hi, b[k].hi);
-        lo = __fmaf_rn(a[k].hi, b[k].hi, -p[k]) + lo;
-        lo = __fmaf_rn(a[k].hi, b[k].lo, lo);
-        lo = __fmaf_rn(a[k].lo, b[k].hi, lo);
+        p[k] = o_mul(a[k].hi, b[k].hi);
+        lo = o_add(o_fma(a[k].hi, b[k].hi, o_neg(p[k])), lo);
+        lo = o_fma(a[k].hi, b[k].lo, lo);
+        lo = o_fma(a[k].lo, b[k].hi, lo);
     }
-    float s = c.hi, e;
+    T s = c.hi, e;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         two_sum(s, p[k], s, e);
-        lo = __fadd_rn(lo, e);
+        lo = o_add(lo, e);
     }
-    return ff{s, lo};
+    return ffT<T>{s, lo};
 }
 // a.b + c, one renormalisation
-__device__ __forceinline__ ff ff_dot3_add(const ff a[3], const ff b[3], ff c) {
-    float p[3], lo = c.lo;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        p[k] = __fmul_rn(a[k].hi, b[k].hi);
-        lo = __fmaf_rn(a[k].hi, b[k].hi, -p[k]) + lo;
-        lo = __fmaf_rn(a[k].hi, b[k].lo, lo);
-        lo = __fmaf_rn(a[k].lo, b[k].hi, lo);
-    }
-    float s = c.hi, e;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        two_sum(s, p[k], s, e);
-        lo = __fadd_rn(lo, e);
-    }
-    return ff_renorm(s, lo);
-}
-// a0.b0 + a1.b1 (two 3-vector dot products) + c, one renormalisation
-__device__ __forceinline__ ff ff_dot3x2_add(const ff a0[3], const ff b0[3], const ff a1[3],
-                                            const ff b1[3], ff c) {
-    float p[6], lo = c.lo;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        p[k] = __fmul_rn(a0[k].hi, b0[k].hi);
-        p[3 + k] = __fmul_rn(a1[k].hi, b1[k].hi);
-        lo = __fmaf_rn(a0[k].hi, b0[k].hi, -p[k]) + lo;
-        lo = __fmaf_rn(a1[k].hi, b1[k].hi, -p[3 + k]) + lo;
-        lo = __fmaf_rn(a0[k].hi, b0[k].lo, lo);
-        lo = __fmaf_rn(a0[k].lo, b0[k].hi, lo);
-        lo = __fmaf_rn(a1[k].hi, b1[k].lo, lo);
-        lo = __fmaf_rn(a1[k].lo, b1[k].hi, lo);
-    }
-    float s = c.hi, e;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        two_sum(s, p[k], s, e);
-        lo = __fadd_rn(lo, e);
-    }
-    return ff_renorm(s, lo);
+template <class T>
+__device__ __forceinline__ ffT<T> ff_dot3_add(const ffT<T> a[3], const ffT<T> b[3], ffT<T> c) {
+    const ffT<T> r = ff_dot3_add_lazy(a, b, c);
+    return ff_renorm(r.hi, r.lo);
 }
 
 // ------------------------------------------------------------ TMA / mbarrier

@@ -246,25 +246,21 @@ __global__ void __launch_bounds__(kSelTPB) k_predict(const Dev d, int also64, in
                 split_ff(ap[q], ah[q], al[q]);
             }
             split_ff(m, mh, ml);
-            JEX w;
-            w.q[0] = make_float4(xh[0], xh[1], xh[2], mh);
-            w.q[1] = make_float4(xl[0], xl[1], xl[2], ml);
-            w.q[2] = make_float4(vh[0], vh[1], vh[2], ah[0]);
-            w.q[3] = make_float4(vl[0], vl[1], vl[2], al[0]);
-            w.q[4] = make_float4(ah[1], ah[2], al[1], al[2]);
-            reinterpret_cast<JEX *>(d.jarr)[jx] = w;
+            const float w[kJEXVals] = {xh[0], xh[1], xh[2], mh, xl[0], xl[1], xl[2], ml,
+                                       vh[0], vh[1], vh[2], ah[0], vl[0], vl[1], vl[2], al[0],
+                                       ah[1], ah[2], al[1], al[2]};
+            jpair_store<kJEXVals>(d.jarr, jx, w);
         } else if (d.precision == NB_FP32) {
             float xh[3], xl[3], vh[3], vl[3];
             for (int q = 0; q < 3; ++q) {
                 split_ff(xp[q], xh[q], xl[q]);
                 split_ff(vp[q], vh[q], vl[q]);
             }
-            J32 w;
-            w.q[0] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(m));
-            w.q[1] = make_float4(xl[0], xl[1], xl[2], __double2float_rn(ap[0]));
-            w.q[2] = make_float4(vh[0], vh[1], vh[2], __double2float_rn(ap[1]));
-            w.q[3] = make_float4(vl[0], vl[1], vl[2], __double2float_rn(ap[2]));
-            reinterpret_cast<J32 *>(d.jarr)[jx] = w;
+            const float w[kJ32Vals] = {xh[0], xh[1], xh[2], __double2float_rn(m),
+                                       xl[0], xl[1], xl[2], __double2float_rn(ap[0]),
+                                       vh[0], vh[1], vh[2], __double2float_rn(ap[1]),
+                                       vl[0], vl[1], vl[2], __double2float_rn(ap[2])};
+            jpair_store<kJ32Vals>(d.jarr, jx, w);
         }
     }
 }
@@ -285,15 +281,13 @@ __global__ void k_pad(const Dev d) {
         j64_set_mass_split(w, 0.0);
         d.jarr64[jx] = w;
         if (d.precision == NB_EX) {
-            JEX e;
-            e.q[0] = make_float4((float)far, (float)far, (float)far, 0.f);
-            e.q[1] = e.q[2] = e.q[3] = e.q[4] = make_float4(0.f, 0.f, 0.f, 0.f);
-            reinterpret_cast<JEX *>(d.jarr)[jx] = e;
+            float w[kJEXVals] = {};
+            w[0] = w[1] = w[2] = (float)far;
+            jpair_store<kJEXVals>(d.jarr, jx, w);
         } else if (d.precision == NB_FP32) {
-            J32 e;
-            e.q[0] = make_float4((float)far, (float)far, (float)far, 0.f);
-            e.q[1] = e.q[2] = e.q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
-            reinterpret_cast<J32 *>(d.jarr)[jx] = e;
+            float w[kJ32Vals] = {};
+            w[0] = w[1] = w[2] = (float)far;
+            jpair_store<kJ32Vals>(d.jarr, jx, w);
         }
     }
 }
