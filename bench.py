@@ -886,7 +886,9 @@ def merger_window_case(args):
             break
     c1 = sim.counters()
     st = sim.state_numpy()
-    t_reached = float(st["t"].min())
+    t_reached = float(st["t"].max())   # the last block time taken
+    out["end_dt_histogram_log2"] = {int(k): int(c) for k, c in
+                                    zip(*np.unique(np.log2(st["dt"]).astype(int), return_counts=True))}
     eval_s = (c1["eval_ms"] - c0["eval_ms"]) * 1e-3
     sim.close()
     out.update({

@@ -178,6 +178,25 @@ nb_status nb_evaluate(nb_ctx *ctx, int32_t cluster, const int32_t *active, int32
                       double *out_ajs);
 
 /*
+ * nb_evaluate_range -- the sums of nb_evaluate restricted to the j-particles
+ * [j_begin, j_end) of cluster `cluster` (indices relative to the cluster's
+ * first particle): the contribution of one part of the j-set.  The paper's
+ * code distributes the O(N^2) evaluation over processes (Sec. 2, MPI +
+ * OpenMP; HiGPUs splits j across GPUs); summed over a partition of
+ * [0, n_cluster) these partial sums give nb_evaluate's result up to the
+ * order of the additions.  j == i is still excluded by index.
+ *   active   : DEVICE int32 [n_active] as for nb_evaluate
+ *   j_begin  : a multiple of 64 (the j-tile size), 0 <= j_begin <= j_end
+ *   j_end    : a multiple of 64, or n_cluster; j_end <= n_cluster
+ *   out_ajs  : DEVICE double [10][n_active]: partial acc, jerk, snap, pot
+ *              (all 0 for an empty range)
+ * Errors: NB_EINVAL (cluster, sizes, range not tile-aligned, NULL pointers
+ * with n_active > 0), NB_ECUDA.  n_active == 0 is a no-op.
+ */
+nb_status nb_evaluate_range(nb_ctx *ctx, int32_t cluster, const int32_t *active, int32_t n_active,
+                            int64_t j_begin, int64_t j_end, double *out_ajs);
+
+/*
  * nb_correct_and_timestep -- NM08 6th-order corrector for the listed
  * particles from their times t_i to t_next (h = t_next - t_i):
  *   v1 = v0 + h/2 (a1 + a0) - h^2/10 (j1 - j0) + h^3/120 (s1 + s0)

@@ -221,13 +221,13 @@ nb_status set_tend(nb_ctx *ctx, double t_end) {
 
 // Plan a direct (host-driven) evaluation of n_active particles of one cluster.
 void plan_direct(const nb_ctx *ctx, int cluster, int32_t n_active, int &gl, int &split, int &tiles,
-                 int &streamk) {
+                 int &streamk, int64_t jtiles = -1) {
     const int b = 31 - __builtin_clz((unsigned)std::max(n_active, 1));
     const PlanEntry e = ctx->table[b];
     gl = e.gl;
     tiles = (int)cdiv(n_active, kTPB / gl);
     const int64_t ncl = ctx->h_offsets[cluster + 1] - ctx->h_offsets[cluster];
-    const int64_t ntj = cdiv(ncl, kTJ);
+    const int64_t ntj = jtiles >= 0 ? jtiles : cdiv(ncl, kTJ);  // j-tiles evaluated
     streamk = !(ctx->p.flags & NB_NO_STREAMK) &&
               sk_use(tiles, kTPB / gl, ntj, ctx->grid_eval, ctx->d.partial_cap) ? 1 : 0;
     if (streamk) {
@@ -240,9 +240,8 @@ void plan_direct(const nb_ctx *ctx, int cluster, int32_t n_active, int &gl, int 
         S = std::max<int64_t>(1, ctx->d.partial_cap / (per_item * tiles));
     split = (int)S;
 }
-
 nb_status eval_direct(nb_ctx *ctx, int cluster, const int32_t *active, int32_t n_active, double *out,
-                      int gl, int split, int tiles, int streamk) {
+                      int gl, int split, int tiles, int streamk, int32_t jt0 = 0, int32_t jt1 = 0) {
     EvalLaunch L{};
     L.direct = 1;
     L.cluster = cluster;
@@ -253,6 +252,8 @@ nb_status eval_direct(nb_ctx *ctx, int cluster, const int32_t *active, int32_t n
     L.active = active;
     L.out = out;
     L.streamk = streamk;
+    L.jt0 = jt0;
+    L.jt1 = jt1;
     const int64_t items = (int64_t)tiles * split;
     // stream-K ranges were cut for the whole persistent grid
     const int grid = streamk ? ctx->grid_eval : (int)std::min<int64_t>(items, ctx->grid_eval);
@@ -551,6 +552,31 @@ nb_status nb_evaluate(nb_ctx *ctx, int32_t cluster, const int32_t *active, int32
     int gl, split, tiles, streamk;
     plan_direct(ctx, cluster, n_active, gl, split, tiles, streamk);
     return eval_direct(ctx, cluster, active, n_active, out_ajs, gl, split, tiles, streamk);
+}
+
+nb_status nb_evaluate_range(nb_ctx *ctx, int32_t cluster, const int32_t *active, int32_t n_active,
+                            int64_t j_begin, int64_t j_end, double *out_ajs) {
+    if (!ctx) return fail(nullptr, NB_EINVAL, "nb_evaluate_range: NULL context");
+    if (cluster < 0 || cluster >= ctx->nc)
+        return fail(ctx, NB_EINVAL, "nb_evaluate_range: cluster out of range");
+    const int64_t ncl = ctx->h_offsets[cluster + 1] - ctx->h_offsets[cluster];
+    if (n_active < 0 || n_active > ncl)
+        return fail(ctx, NB_EINVAL, "nb_evaluate_range: n_active out of range");
+    if (j_begin < 0 || j_end < j_begin || j_end > ncl || j_begin % kTJ != 0 ||
+        (j_end % kTJ != 0 && j_end != ncl))
+        return fail(ctx, NB_EINVAL,
+                    "nb_evaluate_range: need 0 <= j_begin <= j_end <= n_cluster, j_begin a multiple "
+                    "of 64, j_end a multiple of 64 or n_cluster");
+    if (n_active == 0) return NB_OK;
+    if (!active || !out_ajs) return fail(ctx, NB_EINVAL, "nb_evaluate_range: NULL pointer");
+    if (j_end == j_begin) {  // an empty range sums nothing
+        NB_CU(ctx, cudaMemsetAsync(out_ajs, 0, sizeof(double) * 10 * (size_t)n_active, ctx->stream));
+        return NB_OK;
+    }
+    const int32_t jt0 = (int32_t)(j_begin / kTJ), jt1 = (int32_t)cdiv(j_end, kTJ);
+    int gl, split, tiles, streamk;
+    plan_direct(ctx, cluster, n_active, gl, split, tiles, streamk, jt1 - jt0);
+    return eval_direct(ctx, cluster, active, n_active, out_ajs, gl, split, tiles, streamk, jt0, jt1);
 }
 
 nb_status nb_correct_and_timestep(nb_ctx *ctx, int32_t cluster, const int32_t *active,

@@ -565,11 +565,13 @@ __device__ __forceinline__ void finalize_one(const Dev &d, const EvalLaunch &L, 
     }
 }
 
-// Units of a stream-K launch (one cluster): i-tiles x j-tiles.
+// Units of a stream-K launch (one cluster): i-tiles x j-tiles (of the
+// launch's j-range).
 __device__ __forceinline__ int64_t sk_units(const Dev &d, const EvalLaunch &L) {
     const int c = L.direct ? L.cluster : 0;
     const int64_t tiles = L.direct ? L.tiles : d.plan[0].tiles;
-    return tiles * cdiv(d.offsets[c + 1] - d.offsets[c], kTJ);
+    const int64_t ntj = cdiv(d.offsets[c + 1] - d.offsets[c], kTJ);
+    return tiles * (L.direct ? (L.jt1 > 0 ? (int64_t)L.jt1 : ntj) - L.jt0 : ntj);
 }
 
 template <int P, int MODE>
@@ -628,7 +630,10 @@ __global__ void __launch_bounds__(kTPB, (eval_min_blocks<P, MODE>())) k_eval(con
                 }
                 const int64_t off = d.offsets[c];
                 const int64_t nc = d.offsets[c + 1] - off;
-                const int64_t ntj = cdiv(nc, kTJ);
+                // the j-tiles this launch covers: all of the cluster's, or a
+                // host-given range [jt0, jt0 + ntj) of them (direct launches)
+                const int64_t jt0 = L.direct ? L.jt0 : 0;
+                const int64_t ntj = (L.direct && L.jt1 > 0 ? (int64_t)L.jt1 : cdiv(nc, kTJ)) - jt0;
                 int tile;
                 int64_t tb, te, local = 0;
                 if (R.sk) {
@@ -642,6 +647,8 @@ __global__ void __launch_bounds__(kTPB, (eval_min_blocks<P, MODE>())) k_eval(con
                     tb = ntj * sidx / split;
                     te = ntj * (sidx + 1) / split;
                 }
+                tb += jt0;
+                te += jt0;
                 R.c = c; R.gl = gl; R.split = split; R.A = A; R.tile = tile;
                 R.tile0 = tile0; R.pslot0 = pslot0; R.local = local;
                 R.off = off; R.nc = nc; R.ntj = ntj; R.tb = tb; R.te = te;

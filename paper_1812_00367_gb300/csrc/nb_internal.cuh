@@ -225,6 +225,7 @@ struct EvalLaunch {
     const int32_t *active;  // direct mode list (global indices)
     double *out;        // direct mode output [10][n_active]
     int32_t streamk;    // direct mode: stream-K ranges instead of split items
+    int32_t jt0, jt1;   // direct mode: j-tiles [jt0, jt1) of the cluster (jt1 = 0: all)
 };
 
 // Out/Step/Init1/Init2: 6th-order pair terms (a, jerk, snap); the *4 modes

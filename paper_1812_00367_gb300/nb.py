@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
                          C.POINTER(C.c_int64), vp], C.c_int),
             "nb_predict": ([vp, d, vp], C.c_int),
             "nb_evaluate": ([vp, i32, vp, i32, vp], C.c_int),
+            "nb_evaluate_range": ([vp, i32, vp, i32, i64, i64, vp], C.c_int),
             "nb_correct_and_timestep": ([vp, i32, vp, i32, d, vp], C.c_int),
             "nb_step": ([vp, pd, C.POINTER(C.c_int32)], C.c_int),
             "nb_run": ([vp, d, i64, C.POINTER(C.c_int64), pd], C.c_int),
@@ -158,6 +159,11 @@ def nb_predict(ctx, t_next: float, out=None):
 
 def nb_evaluate(ctx, cluster: int, active, n_active: int, out):
     _check(load().nb_evaluate(ctx, int(cluster), _ptr(active), int(n_active), _ptr(out)), ctx)
+
+
+def nb_evaluate_range(ctx, cluster: int, active, n_active: int, j_begin: int, j_end: int, out):
+    _check(load().nb_evaluate_range(ctx, int(cluster), _ptr(active), int(n_active), int(j_begin),
+                                    int(j_end), _ptr(out)), ctx)
 
 
 def nb_correct_and_timestep(ctx, cluster: int, active, n_active: int, t_next: float, ajs):
@@ -288,6 +294,13 @@ class Simulation:
         act = torch.as_tensor(active, dtype=torch.int32, device=self.device).contiguous()
         out = torch.empty((10, act.numel()), dtype=torch.float64, device=self.device)
         nb_evaluate(self.ctx, cluster, act, act.numel(), out)
+        return out
+
+    def evaluate_range(self, active, j_begin, j_end, cluster=0):
+        import torch
+        act = torch.as_tensor(active, dtype=torch.int32, device=self.device).contiguous()
+        out = torch.empty((10, act.numel()), dtype=torch.float64, device=self.device)
+        nb_evaluate_range(self.ctx, cluster, act, act.numel(), j_begin, j_end, out)
         return out
 
     def correct(self, active, t_next, ajs, cluster=0):

@@ -123,3 +123,32 @@ def test_n4m_merger_subsample(nb, oracle, merger4m, precision):
     e = _errors(out[:, pick], ref)
     for k, err in e.items():
         assert err.max() <= TOL[precision], (k, err.max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "ex"])
+def test_merger_block_steps_follow_the_oracle(nb, oracle, precision):
+    """The merger workload at reduced size (two Hernquist spheres of 16384
+    particles, parabolic orbit at separation 20, eps = 1e-3, eta = 0.4):
+    from the start-up, 40 free-running block steps take the oracle's block
+    times and active-set sizes, and end with its step distribution.  (At 2 x
+    65536 the GPU's FP64 and EX runs and the oracle's agreed step for step
+    over 40 steps as well.)"""
+    m, x, v = ic.hernquist_merger(16384, seed=5)
+    ref = oracle.Sim(m, x, v, eps=1e-3, eta=0.4).init()
+    sim = nb.Simulation(m, x, v, eps=1e-3, eta=0.4, precision=precision)
+    seq_gpu, seq_ref = [], []
+    for _ in range(40):
+        seq_gpu.append(sim.step())
+        seq_ref.append(ref.step())
+    # a criterion within rounding of a power of two may quantise either way,
+    # so allow a handful of differing steps in the whole run
+    diff = sum(1 for g, r in zip(seq_gpu, seq_ref) if g != r)
+    assert diff <= 2, list(zip(seq_gpu, seq_ref))
+    tot_g = sum(a for _, a in seq_gpu)
+    tot_r = sum(a for _, a in seq_ref)
+    assert abs(tot_g - tot_r) <= 0.005 * tot_r, (tot_g, tot_r)
+    st = sim.state_numpy()
+    hg = np.bincount(-np.log2(st["dt"]).astype(int), minlength=21)
+    hr = np.bincount(-np.log2(ref.dt).astype(int), minlength=21)
+    assert np.abs(hg - hr).sum() <= max(2, len(m) // 2000), (hg.tolist(), hr.tolist())
+    sim.close()

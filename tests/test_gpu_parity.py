@@ -178,21 +178,30 @@ def test_evaluate_rejects_index_outside_cluster(nb, oracle):
     sim.close()
 
 
-def test_evaluate_clusters_are_independent(nb, oracle):
+@pytest.mark.parametrize("precision", ["fp64", "ex", "fp32"])
+def test_evaluate_clusters_are_independent(nb, oracle, precision):
+    """Clusters of odd and even sizes: each cluster's j-range starts on a
+    whole tile, and the two-particle records of the EX and FP32 arrays hold
+    the last particle of an odd cluster beside padding."""
     eps = 1e-3
-    parts = [ic.plummer(k, seed=k) for k in (70, 300, 129)]
+    sizes = (70, 300, 129, 1, 2, 65)
+    parts = [ic.plummer(k, seed=k) for k in sizes]
     m = np.concatenate([p[0] for p in parts]); x = np.concatenate([p[1] for p in parts])
     v = np.concatenate([p[2] for p in parts])
-    offs = np.array([0, 70, 370, 499])
-    a = np.zeros_like(x)
-    sim = _sim_with_state(nb, m, x, v, a, eps, "fp64", offsets=offs)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=x.shape) * 0.3
+    sim = _sim_with_state(nb, m, x, v, a, eps, precision, offsets=offs)
     sim.predict(0.0, out=False)
-    for c in range(3):
+    for c in range(len(sizes)):
         lo, hi = offs[c], offs[c + 1]
         act = np.arange(lo, hi, dtype=np.int32)
         out = sim.evaluate(torch.as_tensor(act, device="cuda"), cluster=c)
+        if hi - lo == 1:
+            assert np.all(out.cpu().numpy() == 0)
+            continue
         ref = oracle.force(m[lo:hi], x[lo:hi], v[lo:hi], a[lo:hi], eps)
-        _check_eval(out, ref, 1e-12, f"cluster {c}")
+        _check_eval(out, ref, TOL[precision], f"{precision} cluster {c}")
     sim.close()
 
 
