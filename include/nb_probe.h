@@ -52,14 +52,19 @@ nb_status nb_selftest_wait_timeout(double budget_seconds, void *stream);
  * nb_probe_rsqrt -- the evaluation kernel's reciprocal square roots applied
  * elementwise, for accuracy tests against a higher-precision reference:
  *   y[k] = 1 / sqrt(x[k])
- *   which : 0 = the FP64 form the FP64 pair terms use (integer-built FP32
- *               seed, SFU, one third-order step, every product a DFMA);
+ *   which : 0 = the FP64 form the FP64 pair terms use (x scaled into
+ *               [1, 4), SFU seed refined in float-float on the FP32 pipe,
+ *               assembled as a double on the integer pipe, one FP64 Newton
+ *               step: three DFMAs);
  *           1 = the float-float form of the EX pair terms, on x rounded to a
- *               float-float pair, result returned as hi + lo in FP64
+ *               float-float pair, result returned as hi + lo in FP64;
+ *           2 = the earlier five-DFMA FP64 form (integer-built FP32 seed,
+ *               SFU, one third-order step), for comparison
  *   x, y  : DEVICE double [n]; n >= 0
  *   stream: cudaStream_t (NULL = legacy default); asynchronous
- * Valid inputs: x in [2^-126, 2^127] (the seed's FP32 exponent range);
- * outside it the result is undefined.  Errors: NB_EINVAL (which, n < 0, NULL
+ * Valid inputs: forms 1 and 2: x in [2^-126, 2^127] (the seed's FP32
+ * exponent range); form 0: any positive normal double.  Outside these the
+ * result is undefined.  Errors: NB_EINVAL (which, n < 0, NULL
  * pointers with n > 0), NB_ECUDA.
  */
 nb_status nb_probe_rsqrt(int32_t which, const double *x, double *y, int64_t n, void *stream);

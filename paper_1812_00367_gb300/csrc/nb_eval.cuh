@@ -12,10 +12,11 @@
 // with the large alpha terms cancelling inside each pair before it is summed
 // (that keeps the FP32 path within its bound on strongly cancelling sums).
 // Every per-pair operation is a multiply, an add or a fused multiply-add:
-// 52 FP64 instructions per pair on the FP64 path (one exact doubling is done
-// on the integer pipe; the potential m y is summed in float-float on the FP32
-// pipe, NB_FP64_POT_FF).  The 4th-order scheme (Makino & Aarseth 1992) keeps
-// A0, A1 and the potential only (interact4: 31 FP64 instructions per pair).
+// 50 FP64 instructions per pair on the FP64 path (the reciprocal square
+// root's seed is refined on the FP32 and integer pipes, NB_FP64_RSQRT3; one
+// exact doubling is done on the integer pipe; the potential m y is summed in
+// float-float on the FP32 pipe, NB_FP64_POT_FF).  The 4th-order scheme (Makino & Aarseth 1992) keeps
+// A0, A1 and the potential only (interact4: 29 FP64 instructions per pair).
 //
 // Work decomposition: a piece of work is (cluster, i-tile, j-range).  An
 // i-tile holds kTPB / gl active particles; gl lanes of a warp share one i and
@@ -127,7 +128,8 @@ struct Prec<NB_FP64> {
         double m = q1.y;
         r2 = self ? 1.0 : r2;  // selects, not FP64 arithmetic
         m = self ? 0.0 : m;
-        const double y = NB_FP64_ALL_FMA ? rsqrt_f64_fma(r2, i.nz) : rsqrt_f64(r2);
+        const double y = NB_FP64_RSQRT3 ? rsqrt_f64_3(r2, i.nz)
+                         : (NB_FP64_ALL_FMA ? rsqrt_f64_fma(r2, i.nz) : rsqrt_f64(r2));
         const double y2 = mul(i, y, y);
         pot_term(jj, self, m, y, c);               // potential: sum m y
         const double q = mul(i, mul(i, m, y2), y); // m y^3
@@ -147,7 +149,8 @@ struct Prec<NB_FP64> {
         c.s[0] = fma(q, w2x, c.s[0]); c.s[1] = fma(q, w2y, c.s[1]); c.s[2] = fma(q, w2z, c.s[2]);
     }
     // 4th-order pair term (Makino & Aarseth 1992): A0 = q r, A1 = q (v - 3 alpha r);
-    // 31 FP64 instructions (32 without NB_FP64_POT_FF)
+    // 29 FP64 instructions (31 with the 5-operation root, one more without
+    // NB_FP64_POT_FF)
     static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self,
                                                      double eps2, float, Acc &c) {
         const double2 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
@@ -157,7 +160,8 @@ struct Prec<NB_FP64> {
         double m = q1.y;
         r2 = self ? 1.0 : r2;
         m = self ? 0.0 : m;
-        const double y = NB_FP64_ALL_FMA ? rsqrt_f64_fma(r2, i.nz) : rsqrt_f64(r2);
+        const double y = NB_FP64_RSQRT3 ? rsqrt_f64_3(r2, i.nz)
+                         : (NB_FP64_ALL_FMA ? rsqrt_f64_fma(r2, i.nz) : rsqrt_f64(r2));
         const double y2 = mul(i, y, y);
         pot_term(jj, self, m, y, c);
         const double q = mul(i, mul(i, m, y2), y);

@@ -357,6 +357,81 @@ __device__ __forceinline__ double rsqrt_f64_fma(double r2, double neg_zero) {
     return fma(t, p, y0);
 }
 
+// SFU approximation of 1/sqrt (rsqrt.approx.ftz.f32), per lane for float2.
+__device__ __forceinline__ float rsqrt_sfu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 rsqrt_sfu(float2 x) {
+    return make_float2(rsqrt_sfu(x.x), rsqrt_sfu(x.y));
+}
+#ifndef NB_FP64_RSQRT3
+// 1: the FP64 pair terms take 1/sqrt from rsqrt_f64_3 (three FP64
+// operations, the seed refined on the FP32 and integer pipes) instead of
+// rsqrt_f64_fma (five)
+#define NB_FP64_RSQRT3 1
+#endif
+
+// 1/sqrt(x) for a positive normal double x, with three FP64 operations.
+//  - x = 2^(2m) x', x' in [1, 4): an exact exponent shift (integer pipe).
+//  - x' as a float pair xh + xl (24 + 23 significant bits) from its bits:
+//    xh truncated (integer pipe), xl an integer of 23 bits turned into a
+//    float by the 2^23 bias trick (one FP32 subtraction) and scaled.
+//  - y0 = SFU 1/sqrt(xh); residual e = 1 - x' y0^2 from exact FP32 products
+//    (1 - u is exact by Sterbenz, u = xh y0^2 lying within 2^-21 of 1);
+//    c = y0 e (1/2 + 3e/8), the third-order step of the binomial series of
+//    (1 - e)^{-1/2}, so y0 + c is within about 2^-44 of 1/sqrt(x').
+//  - Y = y0 + c rounded to 30 significant bits and assembled as a double on
+//    the integer pipe (its exponent renormalised when the correction crosses
+//    a power of two), Y/2 by an exponent decrement.
+//  - One Newton step in FP64: y' = Y + (Y/2)(1 - x' Y^2); with
+//    |1 - x' Y^2| < 2^-28 its truncation error (3/8)(1 - x' Y^2)^2 is below
+//    2^-57, and the roundings of Y^2 and the last FMA stay near 1 ulp.
+//  - y = 2^-m y' (integer pipe, exact).
+__device__ __forceinline__ double rsqrt_f64_3(double x, double neg_zero) {
+    const int hx = __double2hiint(x), lx = __double2loint(x);
+    const int m = ((((unsigned)hx >> 20) & 0x7ff) - 1023) >> 1;  // floor(exponent / 2)
+    const int hxp = hx - (m << 21);                              // x' = 2^-2m x
+    const int exp_p = (hxp >> 20) - 1023;                        // 0 or 1
+    const double xp = __hiloint2double(hxp, lx);
+    const float xh =
+        __int_as_float((int)__funnelshift_l((unsigned)lx, (unsigned)(hxp - 0x38000000), 3));
+    const float l23 = __fsub_rn(__int_as_float(0x4B000000 | (((unsigned)lx >> 6) & 0x7FFFFFu)),
+                                8388608.0f);                     // next 23 bits, exact
+    const float xl = __fmul_rn(l23, __int_as_float((127 - 46 + exp_p) << 23));
+    const float y0 = rsqrt_sfu(xh);
+    const float p = __fmul_rn(y0, y0);
+    const float pe = __fmaf_rn(y0, y0, -p);
+    const float u = __fmul_rn(xh, p);
+    float ue = __fmaf_rn(xh, p, -u);
+    ue = __fmaf_rn(xh, pe, ue);
+    ue = __fmaf_rn(xl, p, ue);
+    const float e = __fsub_rn(__fsub_rn(1.0f, u), ue);
+    const float c = __fmul_rn(__fmul_rn(y0, e), __fmaf_rn(e, 0.375f, 0.5f));
+    // Y = y0 + c in units of 2^(ey - 29), ey the exponent of y0 (-1 or 0)
+    const int yb = __float_as_int(y0);
+    int ey = ((yb >> 23) & 0xff) - 127;
+    const float cs = __fmaf_rn(c, __int_as_float((127 + 29 - ey) << 23), 12582912.0f);
+    int M = (((yb & 0x7FFFFF) | 0x800000) << 6) + (__float_as_int(cs) - 0x4B400000);
+    if (M >= (1 << 30)) {
+        M >>= 1;
+        ey += 1;
+    } else if (M < (1 << 29)) {
+        M <<= 1;
+        ey -= 1;
+    }
+    const int frac = M - (1 << 29);
+    const int hy = ((ey + 1023) << 20) | (frac >> 9);
+    const int ly = (frac & 0x1FF) << 23;
+    const double Y = __hiloint2double(hy, ly);
+    const double Yh = __hiloint2double(hy - (1 << 20), ly);
+    const double Y2 = fma_rn_f64(Y, Y, neg_zero);
+    const double e2 = fma(-xp, Y2, 1.0);
+    const double yp = fma(Yh, e2, Y);
+    return __hiloint2double(__double2hiint(yp) - (m << 20), __double2loint(yp));
+}
+
 // 2x by adding one to the exponent field on the integer pipe (exact for
 // normal x whose double does not overflow).  Zero, subnormal, infinite and NaN
 // inputs are returned unchanged (a subnormal is then off by a factor two, at
@@ -588,14 +663,6 @@ __device__ __forceinline__ ffT<T> ff_fnma_lazy(ffT<T> b, ffT<T> c, ffT<T> a) {
 // exact square of y0 and FMA-exact products, then y0 (1 + e/2 + 3e^2/8).
 // Lazy form: y0 + corr as it is (|corr| ~ 2^-22 |y0|).  Domain: the normal
 // FP32 range of r2.hi.
-__device__ __forceinline__ float rsqrt_sfu(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float2 rsqrt_sfu(float2 x) {
-    return make_float2(rsqrt_sfu(x.x), rsqrt_sfu(x.y));
-}
 template <class T>
 __device__ __forceinline__ ffT<T> rsqrt_ff(ffT<T> r2) {
     const T y0 = rsqrt_sfu(r2.hi);
@@ -611,16 +678,19 @@ __device__ __forceinline__ ffT<T> rsqrt_ff(ffT<T> r2) {
     else return ff_renorm(y0, corr);
 }
 
-// A positive double y in [2^-74, 2^127] as a float pair, from its bits on the
-// integer pipe (no FP64 instruction): hi = the top 24 significant bits
-// (truncated), lo = the remaining 29 bits rounded to a float.
+// A positive double y in [2^-74, 2^127] as a float pair, from its bits with
+// no FP64 instruction and no int-to-float conversion: hi = the top 24
+// significant bits (truncated), lo = the next 23 bits, an integer turned
+// into a float by the 2^23 bias trick (exact) and scaled by 2^(E - 1069)
+// (the remaining 6 bits dropped: the pair holds y to 2^-47).
 __device__ __forceinline__ ff ff_from_pos_double(double y) {
     const int hi = __double2hiint(y);
     const int lo = __double2loint(y);
     const float yh = __int_as_float((int)__funnelshift_l((unsigned)lo, (unsigned)(hi - 0x38000000), 3));
-    const float scale = __int_as_float(((hi & 0x7ff00000) - (948 << 20)) << 3);  // 2^(E - 1075)
-    const float yl = __fmul_rn(__uint2float_rn((unsigned)lo & 0x1fffffffu), scale);
-    return ff{yh, yl};
+    const float scale = __int_as_float(((hi & 0x7ff00000) - (942 << 20)) << 3);  // 2^(E - 1069)
+    const float l23 = __fsub_rn(__int_as_float(0x4B000000 | (((unsigned)lo >> 6) & 0x7FFFFFu)),
+                                8388608.0f);
+    return ff{yh, __fmul_rn(l23, scale)};
 }
 
 // a.b, unnormalised (hi + lo with every error term in lo)

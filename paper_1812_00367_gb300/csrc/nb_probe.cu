@@ -229,6 +229,8 @@ __global__ void k_rsqrt(int which, const double *x, double *y, int64_t n, double
          k += (int64_t)gridDim.x * blockDim.x) {
         const double v = x[k];
         if (which == 0) {
+            y[k] = NB_FP64_RSQRT3 ? nb::rsqrt_f64_3(v, neg_zero) : nb::rsqrt_f64_fma(v, neg_zero);
+        } else if (which == 2) {
             y[k] = nb::rsqrt_f64_fma(v, neg_zero);
         } else {
             nb::ff r2;
@@ -243,7 +245,7 @@ __global__ void k_rsqrt(int which, const double *x, double *y, int64_t n, double
 
 extern "C" nb_status nb_probe_rsqrt(int32_t which, const double *x, double *y, int64_t n,
                                     void *stream) {
-    if (which != 0 && which != 1) return NB_EINVAL;
+    if (which < 0 || which > 2) return NB_EINVAL;
     if (n < 0 || (n > 0 && (!x || !y))) return NB_EINVAL;
     if (n == 0) return NB_OK;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);

@@ -4,8 +4,9 @@ numpy's long double 1/sqrt (at least 64 significant bits on both hosts),
 over the seed's range x in [2^-126, 2^127] (EX: [2^-100, 2^100], where the
 low float of the input pair is still normal).
 
-FP64 form (integer-built FP32 seed, SFU approximation, one third-order
-step): at most 2 ulp of the correctly rounded result.  Float-float form of
+FP64 form (x scaled into [1, 4), SFU seed refined in float-float and
+assembled as a double on the integer pipe, one FP64 Newton step; and the
+earlier five-DFMA form): at most 2 ulp of the correctly rounded result.  Float-float form of
 the EX path: relative error at most 1e-13 (float-float carries about 48
 bits; the input itself is rounded to a float-float pair).
 """
@@ -47,15 +48,21 @@ def _run(nb, which, x):
     return yt.cpu().numpy()
 
 
-def test_fp64_rsqrt_within_two_ulp(nb):
+@pytest.mark.parametrize("which", [0, 2])
+def test_fp64_rsqrt_within_two_ulp(nb, which):
     x = _inputs()
-    y = _run(nb, 0, x)
+    if which == 0:   # the three-DFMA form covers every positive normal double
+        rng = np.random.default_rng(12)
+        x = np.concatenate([x, np.exp2(rng.uniform(-1021.9, 1022.9, 100000)),
+                            np.exp2(np.arange(-1022, 1023, dtype=np.float64)),
+                            4.0 * (1.0 - rng.uniform(0.0, 1e-6, 10000))])
+    y = _run(nb, which, x)
     ref = 1.0 / np.sqrt(x.astype(np.longdouble))
     ulp = np.spacing(ref.astype(np.float64))
     err = np.abs(y.astype(np.longdouble) - ref) / ulp
     assert np.all(np.isfinite(y))
     assert float(err.max()) <= 2.0, float(err.max())
-    print(f"\nFP64 rsqrt: max {float(err.max()):.3f} ulp, mean {float(err.mean()):.3f} ulp")
+    print(f"\nFP64 rsqrt form {which}: max {float(err.max()):.3f} ulp, mean {float(err.mean()):.3f} ulp")
 
 
 def test_ex_rsqrt_relative_error(nb):
