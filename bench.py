@@ -274,9 +274,10 @@ def gpu_arm(args, ws, rank, local):
     # and the end-to-end number through the C ABI with host buffers.
     k2 = max(1, min(args.steps, args.other_steps))
     rex = run_precision("ex", k2, args.warmup, False) if not args.only_fp64 else None
+    r32x = run_precision("fp32x", k2, args.warmup, False) if not args.only_fp64 else None
     kern = {}
     if not args.only_fp64:
-        for prec in ("fp64", "ex", "fp32"):
+        for prec in ("fp64", "ex", "fp32x", "fp32"):
             kern[prec] = {f"A={a}": eval_rate(nb, torch, dev, m, x, v, prec, a, 2 if a == N else 10)
                           for a in (1024, N)}
     e2e_val, state_bytes = (e2e_run(k2, args.warmup) if not args.only_fp64 else (None, 0))
@@ -323,8 +324,12 @@ def gpu_arm(args, ws, rank, local):
             "block_steps": {"f64": value,
                             "ex": None if rex is None else rate(rex),
                             "ex_speedup_vs_f64": None if rex is None else rate(rex) / rate(r64),
-                            "f32": "not run: FP32 force noise collapses the 6th-order time steps",
-                            "slices_ex": k2},
+                            "f32x": None if r32x is None else rate(r32x),
+                            "f32x_speedup_vs_f64": None if r32x is None else rate(r32x) / rate(r64),
+                            "f32x_note": "float-float acceleration and potential, FP32 jerk and snap",
+                            "f32": "not run: FP32 acceleration errors (up to 4e-7) collapse the "
+                                   "6th-order time steps",
+                            "slices_ex_f32x": k2},
             "eval_kernel": kern,
         },
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
@@ -460,7 +465,7 @@ def config_suite(nb, torch, dev, flush, peak64, ic):
     c3 = {"workload": "Plummer N=2^20, Kroupa-like masses (0.1-100), eps=1e-5: all-active "
                       "evaluation (FP64: 65536 active, 1/16 of it)"}
     samples["c3"] = {"m": m3, "x": x3, "v": v3, "a": a3, "eps": eps3, "gpu": {}}
-    for prec in ("fp64", "ex", "fp32"):
+    for prec in ("fp64", "ex", "fp32x", "fp32"):
         A = 65536 if prec == "fp64" else n3
         sim = _keep_state_sim(nb, m3, x3, v3, a3, eps3, prec)
         rates, (idx, o) = timed_evals(nb, torch, dev, sim, n3, (A,), flush)
@@ -517,7 +522,7 @@ def config_suite(nb, torch, dev, flush, peak64, ic):
                       "eps=1e-3: A active (evenly spread) against all 4,194,304"}
     samples["c5"] = {"m": m5, "x": x5, "v": v5, "a": a5, "eps": 1e-3, "gpu": {}}
     for prec, acts in (("fp64", (64, 1024, 65536)), ("ex", (64, 1024, 65536)),
-                       ("fp32", (65536,))):
+                       ("fp32x", (65536,)), ("fp32", (65536,))):
         sim = _keep_state_sim(nb, m5, x5, v5, a5, 1e-3, prec)
         rates, (idx, o) = timed_evals(nb, torch, dev, sim, n5, acts, flush)
         sim.close()
@@ -679,7 +684,8 @@ def batched_case(args):
 def config3_case(args):
     """Plummer N = 2^20 with Kroupa-like masses, eps = 1e-5: evaluation
     throughput per arithmetic, a/j/s/pot errors on a 4096-particle subsample
-    against the FP64 oracle, and energy drift over a short block-step run."""
+    against the FP64 oracle (whose evaluation of the subsample is timed: this
+    case's CPU-baseline leg), and energy drift over a short block-step run."""
     import torch
     from oracle import nb_oracle
     from paper_1812_00367_gb300 import build as nbbuild
@@ -698,7 +704,7 @@ def config3_case(args):
     t_oracle = time.perf_counter() - t0
     out = {"case": "config3", "n": n, "eps": eps, "subsample": len(sub),
            "oracle_seconds_subsample": t_oracle, "oracle_threads": nb_oracle.num_threads()}
-    for prec in ("fp64", "ex", "fp32"):
+    for prec in ("fp64", "ex", "fp32x", "fp32"):
         sim = nb.Simulation(m, x, v, eps=eps, precision=prec, keep_state=True)
         st = {"m": m, "x": x, "v": v, "a": np.zeros((n, 3)), "j": np.zeros((n, 3)),
               "s": np.zeros((n, 3)), "c": np.zeros((n, 3)), "t": np.zeros(n),
@@ -756,21 +762,20 @@ def _lagrangian_radii(m, x, fractions=(0.1, 0.5, 0.9)):
 
 
 def config2_check(args):
-    """The benchmark's integration run to t = 0.25 on the GPU (FP64 and EX)
-    and by the CPU oracle: block steps, interactions, energy error, momentum
-    and Lagrangian radii at the end (block-step runs diverge per particle, so
-    the comparison is statistical)."""
+    """The benchmark's integration run to t = 0.25 on the GPU (FP64, EX and
+    FP32X by default) and, as this case's CPU-baseline leg, by the oracle
+    (timed): block steps, interactions, energy error, momentum and
+    Lagrangian radii at the end (block-step runs diverge per particle, so the
+    comparison is statistical)."""
     import torch
-    from oracle import nb_oracle
     from paper_1812_00367_gb300 import build as nbbuild
     from paper_1812_00367_gb300 import ic, nb
     nbbuild.build()
     nb.load()
-    nb_oracle.build()
     dev = torch.device("cuda", 0)
     m, x, v = ic.plummer(N, seed=SEED)
     out = {"case": "config2_check", "n": N, "t_end": T_END}
-    for prec in ("fp64", "ex"):
+    for prec in args.c2_precisions.split(","):
         sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX, precision=prec)
         ek0, ep0, P0, L0 = sim.energy(0.0)
         steps, inter, sec = _timed_run(sim, torch, dev, T_END)
@@ -783,6 +788,11 @@ def config2_check(args):
                      "lagrangian_radii_10_50_90": _lagrangian_radii(m, st["x"]),
                      "dt_underflows": sim.counters()["dt_underflows"]}
         sim.close()
+    if args.c2_skip_oracle:
+        print(json.dumps(out))
+        return
+    from oracle import nb_oracle
+    nb_oracle.build()
     t0 = time.perf_counter()
     ref = nb_oracle.Sim(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX).init()
     e0 = ref.energy(0.0)
@@ -1004,7 +1014,7 @@ def energy_case(args):
     m, x, v = ic.plummer(N, seed=SEED)
     out = {"case": "energy", "n": N, "active": N, "seconds_target": args.energy_seconds}
     stream = torch.cuda.current_stream(dev)
-    for prec in ("fp64", "ex", "fp32"):
+    for prec in ("fp64", "ex", "fp32x", "fp32"):
         for order in (6, 4):
             sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA, dt_min=DT_MIN, dt_max=DT_MAX,
                                 precision=prec, keep_state=True, order=order)
@@ -1143,11 +1153,14 @@ def main():
     ap.add_argument("--t-warm", type=float, default=1.0 / 256)
     ap.add_argument("--t-run", type=float, default=1.0 / 64)
     ap.add_argument("--c3-active", type=int, default=65536)
+    ap.add_argument("--c2-precisions", default="fp64,ex,fp32x", help="--case config2-check")
+    ap.add_argument("--c2-skip-oracle", action="store_true",
+                    help="--case config2-check: GPU runs only (no CPU-baseline leg)")
     ap.add_argument("--c3-full-fp64", action="store_true")
     ap.add_argument("--c3-run-t", type=float, default=0.0)
     ap.add_argument("--c3-run-precisions", default="ex")
     ap.add_argument("--merger-active", type=int, default=65536)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "ex", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "ex", "fp32", "fp32x"])
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--active", type=int, default=N)
     ap.add_argument("--reps", type=int, default=2)

@@ -55,8 +55,12 @@ typedef enum {
 typedef enum {
     NB_FP64 = 0, /* double precision throughout */
     NB_EX = 1,   /* float-float (hi + lo single-precision pair) arithmetic */
-    NB_FP32 = 2  /* relative coordinates from split hi/lo singles, FP32 force
+    NB_FP32 = 2, /* relative coordinates from split hi/lo singles, FP32 force
                     math, FP32 sums over j-chunks promoted to FP64 */
+    NB_FP32X = 3 /* acceleration and potential in float-float (as NB_EX), jerk
+                    and snap in FP32 (as NB_FP32): the 6th-order step
+                    criterion needs the acceleration to about 1e-8, jerk and
+                    snap only to about 1e-5 */
 } nb_precision;
 
 /* nb_params.flags */

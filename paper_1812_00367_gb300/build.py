@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libnb.so")
 SOURCES = ["nb_api.cu", "nb_kernels.cu", "nb_eval_fp64.cu", "nb_eval_ex.cu", "nb_eval_fp32.cu",
-           "nb_probe.cu", "nb_noalloc.cu"]
+           "nb_eval_fp32x.cu", "nb_probe.cu", "nb_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -17,9 +17,11 @@ namespace nb {
 cudaError_t launch_eval_fp64(const Dev &, int, const EvalLaunch &, int, cudaStream_t);
 cudaError_t launch_eval_ex(const Dev &, int, const EvalLaunch &, int, cudaStream_t);
 cudaError_t launch_eval_fp32(const Dev &, int, const EvalLaunch &, int, cudaStream_t);
+cudaError_t launch_eval_fp32x(const Dev &, int, const EvalLaunch &, int, cudaStream_t);
 int occupancy_fp64(int);
 int occupancy_ex(int);
 int occupancy_fp32(int);
+int occupancy_fp32x(int);
 cudaError_t launch_unpack64(const Dev &d, double *out, cudaStream_t st);
 cudaError_t launch_plan_ex(const Dev &d, int mode_init, int count, cudaStream_t st);
 
@@ -30,6 +32,7 @@ cudaError_t launch_eval(const Dev &d, int mode, const EvalLaunch &L, int grid, c
     case NB_FP64: return launch_eval_fp64(d, mode, L, grid, st);
     case NB_EX: return launch_eval_ex(d, mode, L, grid, st);
     case NB_FP32: return launch_eval_fp32(d, mode, L, grid, st);
+    case NB_FP32X: return launch_eval_fp32x(d, mode, L, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -38,6 +41,7 @@ int eval_occupancy(int precision, int mode) {
     switch (precision) {
     case NB_FP64: return occupancy_fp64(mode);
     case NB_EX: return occupancy_ex(mode);
+    case NB_FP32X: return occupancy_fp32x(mode);
     default: return occupancy_fp32(mode);
     }
 }
@@ -331,7 +335,7 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     if (!(p->eta > 0.0) || !(p->eta_init > 0.0)) return fail(nullptr, NB_EINVAL, "nb_init: eta <= 0");
     if (!is_pow2(p->dt_min) || !is_pow2(p->dt_max) || p->dt_min > p->dt_max)
         return fail(nullptr, NB_EINVAL, "nb_init: dt_min/dt_max must be powers of two, min <= max");
-    if (p->precision < NB_FP64 || p->precision > NB_FP32)
+    if (p->precision < NB_FP64 || p->precision > NB_FP32X)
         return fail(nullptr, NB_EINVAL, "nb_init: unknown precision");
     if (p->order != 0 && p->order != 4 && p->order != 6)
         return fail(nullptr, NB_EINVAL, "nb_init: order must be 4 or 6 (0 = 6)");
@@ -424,7 +428,8 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
 
     int64_t *d_offs = nullptr, *d_jofs = nullptr, *d_cb = nullptr, *d_ce = nullptr;
     int32_t *d_ccl = nullptr, *d_cc0 = nullptr;
-    size_t jbytes = p->precision == NB_FP64 ? sizeof(J64) : (p->precision == NB_EX ? sizeof(JEX) : sizeof(J32));
+    size_t jbytes = p->precision == NB_FP64 ? sizeof(J64)
+                    : (p->precision == NB_FP32 ? sizeof(J32) : sizeof(JEX));  // EX, FP32X
 #define ALLOC(ptr, cnt)                                                                      \
     do {                                                                                     \
         cudaError_t ee = dalloc(ctx, &(ptr), (cnt));                                         \

@@ -486,6 +486,156 @@ struct Prec<NB_FP32> {
     }
 };
 
+// ==================================================================== FP32X
+// The acceleration and the potential in float-float (the EX pair terms'
+// arithmetic), jerk and snap in FP32 (the FP32 pair terms' arithmetic, on
+// the float-float relative position and coefficients rounded to FP32): the
+// 6th-order step criterion interpolates a^(3..5) from differences of the
+// accelerations at both step ends over h^3..h^5 and needs the acceleration
+// to about 1e-8, the jerk and snap only to about 1e-5.  Two j per thread and
+// step on packed f32x2 lanes, from the EX records.
+template <>
+struct Prec<NB_FP32X> {
+    using J = JEXP;
+    static constexpr int kPerRec = 2;
+    struct I {  // both lanes equal
+        ff2 x[3];
+        float2 vh[3], vl[3], a[3];
+    };
+    struct Acc {
+        ff2 a[3], p;         // float-float sums, renormalised per j-tile
+        float2 j[3], s[3];   // FP32 tile sums, lane l for the j of parity l
+        float cj[3], cs[3];  // FP32 chunk sums, promoted to FP64 every kFp32FlushTiles tiles
+    };
+    static __device__ __forceinline__ I load_i(const J *jarr, int64_t k) {
+        const float *f = reinterpret_cast<const float *>(jarr + (k >> 1)) + (k & 1);
+        I r;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            r.x[q] = ff2{f2s(f[2 * q]), f2s(f[2 * (4 + q)])};
+            r.vh[q] = f2s(f[2 * (8 + q)]);
+            r.vl[q] = f2s(f[2 * (12 + q)]);
+        }
+        r.a[0] = f2s(f[2 * 11]);
+        r.a[1] = f2s(f[2 * 16]);
+        r.a[2] = f2s(f[2 * 17]);
+        return r;
+    }
+    static __device__ __forceinline__ void zero(Acc &c) {
+        const float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            c.a[k] = ff2{z, z};
+            c.j[k] = c.s[k] = z;
+            c.cj[k] = c.cs[k] = 0.f;
+        }
+        c.p = ff2{z, z};
+    }
+    // float-float relative positions (normalised), FP32 relative velocities
+    // from the hi/lo split
+    static __device__ __forceinline__ void rel(const I &i, const J &jj, ff2 r[3], float2 v[3]) {
+        const float4 q0 = jj.q[0], q1 = jj.q[1], q2 = jj.q[2], q3 = jj.q[3];
+        const float4 q4 = jj.q[4], q5 = jj.q[5], q6 = jj.q[6], q7 = jj.q[7];
+        r[0] = ff_sub(ff2{lo2(q0), lo2(q2)}, i.x[0]);
+        r[1] = ff_sub(ff2{hi2(q0), hi2(q2)}, i.x[1]);
+        r[2] = ff_sub(ff2{lo2(q1), lo2(q3)}, i.x[2]);
+        v[0] = add2(sub2(lo2(q4), i.vh[0]), sub2(lo2(q6), i.vl[0]));
+        v[1] = add2(sub2(hi2(q4), i.vh[1]), sub2(hi2(q6), i.vl[1]));
+        v[2] = add2(sub2(lo2(q5), i.vh[2]), sub2(lo2(q7), i.vl[2]));
+    }
+    // the float-float part: y, y^2 and q = m y^3; the sums of a and pot
+    static __device__ __forceinline__ void acc_part(const ff2 r[3], ff2 r2, ff2 m, Acc &c, float2 &y2f,
+                                                    float2 &qf) {
+        const ff2 y = rsqrt_ff(r2);
+        const ff2 y2 = ff_sqr_lazy(y);
+        const ff2 my = ff_mul_lazy(m, y);
+        const ff2 q = ff_mul_lazy(my, y2);
+        ff_add_lazy(c.p, my);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ff_fma_acc_lazy(c.a[k], q, r[k]);
+        y2f = y2.hi;  // the lazy pair's high part: the product rounded to FP32
+        qf = q.hi;
+    }
+    static __device__ __forceinline__ void interact(const I &i, const J &jj, bool self0, bool self1,
+                                                    ff2 eps2, Acc &c) {
+        ff2 r[3];
+        float2 v[3];
+        rel(i, jj, r, v);
+        const float2 aa[3] = {sub2(hi2(jj.q[5]), i.a[0]), sub2(lo2(jj.q[8]), i.a[1]),
+                              sub2(hi2(jj.q[8]), i.a[2])};
+        ff2 r2 = ff_dot3_add_lazy(r, r, eps2);
+        ff2 m{hi2(jj.q[1]), hi2(jj.q[3])};
+        Prec<NB_EX>::exclude_self(self0, self1, r2, m);
+        float2 y2f, qf;
+        acc_part(r, r2, m, c, y2f, qf);
+        const float2 rf[3] = {r[0].hi, r[1].hi, r[2].hi};
+        const float2 rv = fma2(rf[0], v[0], fma2(rf[1], v[1], mul2(rf[2], v[2])));
+        const float2 w = fma2(v[0], v[0], fma2(v[1], v[1], fma2(v[2], v[2],
+                         fma2(rf[0], aa[0], fma2(rf[1], aa[1], mul2(rf[2], aa[2]))))));
+        const float2 al = mul2(rv, y2f);
+        const float2 ze = mul2(w, y2f);
+        const float2 nal3 = mul2(f2s(-3.f), al);
+        const float2 nbe3 = mul2(f2s(-3.f), fma2(al, al, ze));
+        const float2 nal6 = add2(nal3, nal3);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float2 w1 = fma2(nal3, rf[k], v[k]);
+            const float2 w2 = fma2(nbe3, rf[k], fma2(nal6, w1, aa[k]));
+            c.j[k] = fma2(qf, w1, c.j[k]);
+            c.s[k] = fma2(qf, w2, c.s[k]);
+        }
+    }
+    static __device__ __forceinline__ void interact4(const I &i, const J &jj, bool self0, bool self1,
+                                                     ff2 eps2, Acc &c) {
+        ff2 r[3];
+        float2 v[3];
+        rel(i, jj, r, v);
+        ff2 r2 = ff_dot3_add_lazy(r, r, eps2);
+        ff2 m{hi2(jj.q[1]), hi2(jj.q[3])};
+        Prec<NB_EX>::exclude_self(self0, self1, r2, m);
+        float2 y2f, qf;
+        acc_part(r, r2, m, c, y2f, qf);
+        const float2 rf[3] = {r[0].hi, r[1].hi, r[2].hi};
+        const float2 nal3 =
+            mul2(f2s(-3.f), mul2(fma2(rf[0], v[0], fma2(rf[1], v[1], mul2(rf[2], v[2]))), y2f));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c.j[k] = fma2(qf, fma2(nal3, rf[k], v[k]), c.j[k]);
+    }
+    // End of a j-tile: renormalise the float-float sums, add both lanes of
+    // the FP32 tile sums into the chunk sums.
+    static __device__ __forceinline__ void tile_done(Acc &c) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            c.a[k] = ff_renorm(c.a[k].hi, c.a[k].lo);
+            c.cj[k] += c.j[k].x + c.j[k].y;
+            c.cs[k] += c.s[k].x + c.s[k].y;
+            c.j[k] = c.s[k] = make_float2(0.f, 0.f);
+        }
+        c.p = ff_renorm(c.p.hi, c.p.lo);
+    }
+    // Promote the FP32 chunk sums of jerk and snap into the FP64 totals
+    // (t64[q * st], q = 3..8) and restart them.
+    static __device__ __forceinline__ void flush(Acc &c, double *t64, int st) {
+        tile_done(c);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            t64[(3 + k) * st] += (double)c.cj[k];
+            t64[(6 + k) * st] += (double)c.cs[k];
+            c.cj[k] = c.cs[k] = 0.f;
+        }
+    }
+    static __device__ __forceinline__ void finish(Acc &c, double *t64, int st, double o[10]) {
+        flush(c, t64, st);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            o[k] = Prec<NB_EX>::to_d(c.a[k]);
+            o[3 + k] = t64[(3 + k) * st];
+            o[6 + k] = t64[(6 + k) * st];
+        }
+        o[9] = -Prec<NB_EX>::to_d(c.p);
+    }
+};
+
 // ================================================================ kernel
 // Per-arithmetic launch configuration of the evaluation kernel.
 template <int P>
@@ -514,6 +664,12 @@ struct EvalCfg<NB_FP32> {
     static constexpr int stages = NB_FP32_STAGES;
     static constexpr int min_blocks = NB_FP32_MIN_BLOCKS;
     static constexpr bool t64_smem = NB_FP32_T64_SMEM != 0;
+};
+template <>
+struct EvalCfg<NB_FP32X> {
+    static constexpr int stages = kStages;
+    static constexpr int min_blocks = NB_FP32X_MIN_BLOCKS;
+    static constexpr bool t64_smem = true;
 };
 
 // One piece of work, described by thread 0 for the whole CTA.
@@ -732,6 +888,16 @@ __global__ void __launch_bounds__(kTPB, (eval_min_blocks<P, MODE>())) k_eval(con
                     for (int k = jsub; k < kRecs; k += gl)
                         T::interact(me, tl[k], jbase + 2 * k == ji, jbase + 2 * k + 1 == ji,
                                     eps2f2, acc);
+                } else if constexpr (P == NB_FP32X && uses_order4_terms(MODE)) {
+#pragma unroll 1
+                    for (int k = jsub; k < kRecs; k += gl)
+                        T::interact4(me, tl[k], jbase + 2 * k == ji, jbase + 2 * k + 1 == ji,
+                                     eps2ff2, acc);
+                } else if constexpr (P == NB_FP32X) {
+#pragma unroll 1
+                    for (int k = jsub; k < kRecs; k += gl)
+                        T::interact(me, tl[k], jbase + 2 * k == ji, jbase + 2 * k + 1 == ji,
+                                    eps2ff2, acc);
                 } else if constexpr (P == NB_EX && uses_order4_terms(MODE)) {
 #pragma unroll 1
                     for (int k = jsub; k < kRecs; k += gl)
@@ -751,7 +917,7 @@ __global__ void __launch_bounds__(kTPB, (eval_min_blocks<P, MODE>())) k_eval(con
                     for (int k = jsub; k < kTJ; k += gl)
                         T::interact(me, tl[k], jbase + k == ji, eps2, eps2f, acc);
                 }
-                if constexpr (P == NB_FP32) {
+                if constexpr (P == NB_FP32 || P == NB_FP32X) {
                     if ((tt - tb + 1) % kFp32FlushTiles == 0) T::flush(acc, t64, t64st);
                     else T::tile_done(acc);
                 } else if constexpr (P == NB_EX && MODE != kModePot) {

@@ -52,6 +52,9 @@ constexpr int kTJ = 64;        // j-particles per shared-memory tile
 #ifndef NB_EX_MIN_BLOCKS
 #define NB_EX_MIN_BLOCKS NB_EVAL_MIN_BLOCKS
 #endif
+#ifndef NB_FP32X_MIN_BLOCKS
+#define NB_FP32X_MIN_BLOCKS NB_EVAL_MIN_BLOCKS
+#endif
 #ifndef NB_EX4_MIN_BLOCKS
 #define NB_EX4_MIN_BLOCKS 3
 #endif
@@ -104,7 +107,7 @@ __host__ __device__ inline void j64_set_mass_split(J64 &w, double m) {
     (void)m;
 #endif
 }
-// EX: 80 bytes per particle (hi/lo single pairs), stored as records of two
+// EX and FP32X: 80 bytes per particle (hi/lo single pairs), stored as records of two
 // particles whose values interleave like the FP32 records below: value f of
 // lane l of record r is float r * 40 + 2 f + l, f in the order
 //   xh, yh, zh, mh, xl, yl, zl, ml, vxh, vyh, vzh, axh, vxl, vyl, vzl, axl,
@@ -176,7 +179,7 @@ struct Dev {
     // state (caller-owned), SoA [3][n]
     double *m, *x, *v, *a, *j, *s, *c, *t, *dt, *pot;
     // predicted j-arrays
-    void *jarr;        // precision-specific (J64 / JEX / J32)
+    void *jarr;        // precision-specific (J64 / JEX (EX, FP32X) / J32)
     J64 *jarr64;       // FP64 copy (energy, nb_predict output); == jarr for FP64
     // select
     double *chunk_min;

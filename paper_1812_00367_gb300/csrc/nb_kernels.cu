@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kSelTPB) k_predict(const Dev d, int also64, in
             j64_set_mass_split(w, m);
             d.jarr64[jx] = w;
         }
-        if (d.precision == NB_EX) {
+        if (d.precision == NB_EX || d.precision == NB_FP32X) {
             float xh[3], xl[3], vh[3], vl[3], ah[3], al[3], mh, ml;
             for (int q = 0; q < 3; ++q) {
                 split_ff(xp[q], xh[q], xl[q]);
@@ -280,7 +280,7 @@ __global__ void k_pad(const Dev d) {
         w.q[2] = w.q[3] = w.q[4] = make_double2(0.0, 0.0);
         j64_set_mass_split(w, 0.0);
         d.jarr64[jx] = w;
-        if (d.precision == NB_EX) {
+        if (d.precision == NB_EX || d.precision == NB_FP32X) {
             float w[kJEXVals] = {};
             w[0] = w[1] = w[2] = (float)far;
             jpair_store<kJEXVals>(d.jarr, jx, w);

@@ -21,8 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libnb.so")
 HEADERS = [os.path.join(os.path.dirname(_HERE), "include", h) for h in ("nb.h", "nb_probe.h")]
 
-NB_FP64, NB_EX, NB_FP32 = 0, 1, 2
-PRECISIONS = {"fp64": NB_FP64, "ex": NB_EX, "fp32": NB_FP32}
+NB_FP64, NB_EX, NB_FP32, NB_FP32X = 0, 1, 2, 3
+PRECISIONS = {"fp64": NB_FP64, "ex": NB_EX, "fp32": NB_FP32, "fp32x": NB_FP32X}
 NB_INIT_KEEP_STATE = 1
 NB_TIME_EVAL = 2
 NB_NO_STREAMK = 4
