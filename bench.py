@@ -978,7 +978,7 @@ def order4_case(args):
     m, x, v = ic.plummer(N, seed=SEED)
     out = {"case": "order4", "n": N, "eps": EPS, "eta4": ETA4, "eta6": ETA,
            "t_warm": args.t_warm, "t_run": args.t_run}
-    runs = [("fp64", 4), ("ex", 4), ("fp32", 4), ("fp64", 6)]
+    runs = [("fp64", 4), ("ex", 4), ("fp32x", 4), ("fp32", 4), ("fp64", 6), ("fp32x", 6)]
     for prec, order in runs:
         sim = nb.Simulation(m, x, v, eps=EPS, eta=ETA4 if order == 4 else ETA, dt_min=DT_MIN,
                             dt_max=DT_MAX, precision=prec, order=order, time_eval=True)

@@ -29,7 +29,7 @@ def _write_table(path, precision, gl_of_bucket, target):
             f.write(f"{gl_of_bucket(b)} {target}\n")
 
 
-@pytest.mark.parametrize("precision", ["fp64", "ex"])
+@pytest.mark.parametrize("precision", ["fp64", "ex", "fp32x"])
 def test_batched_equals_single_bit_for_bit(nb, tmp_path, precision):
     """Each cluster of a batch ends bit-identical to the same cluster run alone
     (same plan table; deterministic reductions)."""
