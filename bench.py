@@ -45,12 +45,13 @@ WORKLOAD = (f"Plummer N={N}, equal masses, Henon units, eps={EPS:g}, block steps
             f"dt in [2^-20, 2^-3], eta={ETA}, integrated to t={T_END} in slices of 1/64")
 
 # DRAM traffic of the FP64 step-evaluation kernel, bytes per launch: the mean
-# of dram__bytes_read.sum + dram__bytes_write.sum over every k_eval<FP64, step>
-# launch of one ncu capture of this workload (summary and command in
-# profiles/).  It holds for the kernel sources it was taken on (SHA-256 of
-# EVAL_SOURCES below); after any change to them it is reported as null.
-EVAL_TRAFFIC = {"bytes_per_launch": 6963899, "launches": 1520,
-                "sources_sha256": "4cc249527fb3be7ec47a112ce9b0439b3b8159b49f4c80cd6be6c76313055647"}
+# of dram__bytes_read.sum + dram__bytes_write.sum over five consecutive
+# k_eval<FP64, step> launches (block steps 301-305 of the 1/64-slice run) of
+# one ncu capture of this workload (summary and command in profiles/).  It
+# holds for the kernel sources it was taken on (SHA-256 of EVAL_SOURCES
+# below); after any change to them it is reported as null.
+EVAL_TRAFFIC = {"bytes_per_launch": 7357235, "launches": 5,
+                "sources_sha256": "db73fe8189012792f8a0aa6959e9efdf53564a4a9c72b65d211cdab13d474b93"}
 EVAL_SOURCES = ("nb_eval.cuh", "nb_eval_fp64.cu", "nb_step.cuh", "nb_internal.cuh")
 
 
@@ -316,7 +317,7 @@ def gpu_arm(args, ws, rank, local):
                      "peak_source": "FP64 FMA probe (nb_probe_fma_peak) in this run: best of 5 runs before and 5 after the timed region",
                      "frac": None if achieved is None else achieved / peak64,
                      "traffic": eval_traffic(),
-                     "traffic_unit": "DRAM bytes per launch (ncu), null if the kernel changed",
+                     "traffic_unit": "DRAM bytes per launch (ncu, mean of 5 launches), null if the kernel changed",
                      "avg_launch_ms": eval_avg_ms, "launches": r64["eval_launches"],
                      "share_of_step_time": r64["eval_ms"] / r64["ms"] if r64["ms"] else None,
                      "flops_per_interaction": FLOPS_PER_INTERACTION},
