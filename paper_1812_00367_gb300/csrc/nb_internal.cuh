@@ -295,14 +295,21 @@ __host__ __device__ inline int64_t choose_split(int64_t tiles, int64_t ntj, int6
     s0 = s0 < 1 ? 1 : (s0 > smax ? smax : s0);
     if (grid <= 0) return s0;
     // efficiency items / (waves * grid), compared by cross-multiplication in
-    // integers (FP64 divisions are slow on this part, and this runs in one
-    // thread of the planner)
+    // integers.  Within one wave count w the efficiency grows with S, so only
+    // the largest S of each w can win: visit the wave counts of the window
+    // (a few) instead of every S (a few hundred 64-bit divisions in the
+    // planner's single thread); stepping w upwards and keeping only strict
+    // improvements returns the smallest S of the best efficiency.
     int64_t best = s0, best_items = 0, best_slots = 1;
     const int64_t lo = s0 / 2 > 1 ? s0 / 2 : 1;
     const int64_t hi = 2 * s0 < smax ? 2 * s0 : smax;
-    for (int64_t s = lo; s <= hi; ++s) {
-        const int64_t items = tiles * s;
-        const int64_t slots = cdiv(items, grid) * grid;
+    const int64_t t = tiles > 0 ? tiles : 1;
+    const int64_t w_lo = cdiv(t * lo, grid), w_hi = cdiv(t * hi, grid);
+    for (int64_t w = w_lo; w <= w_hi; ++w) {
+        int64_t s = (w * grid) / t;  // the largest S with t S <= w grid
+        s = s > hi ? hi : s;
+        if (s < lo || t * s <= (w - 1) * grid) continue;  // no S of the window fills w waves
+        const int64_t items = t * s, slots = w * grid;
         if (items * best_slots > best_items * slots) {
             best_items = items;
             best_slots = slots;

@@ -68,10 +68,32 @@ static void check_streamk(int64_t tiles, int64_t ntj, int64_t G) {
     }
 }
 
+// The split chooser's choice by exhaustive search: every S of the window,
+// the smallest of the best wave efficiency.
+static int64_t split_by_scan(int64_t tiles, int64_t ntj, int64_t target, int64_t grid) {
+    const int64_t smax = std::max<int64_t>(1, ntj / kMinTilesPerItem);
+    const int64_t s0 = std::min(std::max<int64_t>(1, cdiv(target, tiles)), smax);
+    const int64_t lo = std::max<int64_t>(1, s0 / 2), hi = std::min(2 * s0, smax);
+    int64_t best = s0, bi = 0, bs = 1;
+    for (int64_t s = lo; s <= hi; ++s) {
+        const int64_t items = tiles * s, slots = cdiv(items, grid) * grid;
+        if (items * bs > bi * slots) {
+            bi = items;
+            bs = slots;
+            best = s;
+        }
+    }
+    return best;
+}
+
 // S in [1, ntj / kMinTilesPerItem] (or 1), within [S0/2, 2 S0] of the target's
-// S0, and no S in that window fills whole waves better.
+// S0, and no S in that window fills whole waves better; the same S as an
+// exhaustive scan of the window.
 static void check_split(int64_t tiles, int64_t ntj, int64_t target, int64_t grid) {
     const int64_t S = choose_split(tiles, ntj, target, grid);
+    CHECK(S == split_by_scan(tiles, ntj, target, grid), "S=%lld scan %lld (tiles %lld ntj %lld target %lld grid %lld)",
+          (long long)S, (long long)split_by_scan(tiles, ntj, target, grid), (long long)tiles,
+          (long long)ntj, (long long)target, (long long)grid);
     const int64_t smax = std::max<int64_t>(1, ntj / kMinTilesPerItem);
     CHECK(S >= 1 && S <= smax, "S=%lld smax=%lld", (long long)S, (long long)smax);
     int64_t s0 = std::min(std::max<int64_t>(1, cdiv(target, tiles)), smax);
@@ -106,6 +128,13 @@ int main() {
             ++cases;
         }
         check_split(tiles, ntj, uniform(1, 16 * G), G);
+        ++cases;
+    }
+    // the shapes of tiny active sets against large clusters (the planner's
+    // common case in block steps): one to a few i-tiles, many j-tiles
+    for (int r = 0; r < 2000; ++r) {
+        const int64_t G = grids[uniform(0, 3)];
+        check_split(uniform(1, 64), uniform(1, 70000), uniform(1, 16 * G), G);
         ++cases;
     }
     std::printf("ok %d\n", cases);
