@@ -49,12 +49,14 @@ def trajectory_envelope(oracle):
     import numpy as np
 
     def make(m, x, v, eps, h, steps, level, seeds=(1, 2)):
+        # level: one relative size for a, jerk and snap, or a triple
+        ea, ej, es = level if isinstance(level, (tuple, list)) else (level, level, level)
         ref = oracle.Sim(m, x, v, eps=eps, dt_min=h, dt_max=h).init()
         ref.run(steps * h)
         env_x = np.zeros(len(m))
         env_v = np.zeros(len(m))
         for s in seeds:
-            o = oracle.Sim(m, x, v, eps=eps, dt_min=h, dt_max=h).set_noise(level, level, level, s)
+            o = oracle.Sim(m, x, v, eps=eps, dt_min=h, dt_max=h).set_noise(ea, ej, es, s)
             o.init()
             o.run(steps * h)
             env_x = np.maximum(env_x, _rel_rows(o.x, ref.x))

@@ -31,6 +31,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "ex": 1e-10}
+# per quantity (a, jerk, snap, pot); FP32X: float-float acceleration and
+# potential, FP32 jerk and snap
+TOLQ = {"fp64": (1e-12, 1e-12, 1e-12, 1e-12), "ex": (1e-10, 1e-10, 1e-10, 1e-10),
+        "fp32x": (1e-10, 2e-5, 2e-5, 1e-10)}
 # shared-step sizes: single and pair clusters, a j-tile -1/+1, several tiles
 # with a ragged tail, and the largest size of the 512-cluster workload
 SHARED_SIZES = [1, 2, 63, 65, 4097, 16384, 300, 1000]
@@ -93,14 +97,14 @@ def shared_reference(oracle, trajectory_envelope):
         r = oracle.Sim(*args, eps=eps, dt_min=h, dt_max=h).init()
         start = {f: getattr(r, f).copy() for f in ("a", "j", "s", "pot")}
         env = {}
-        for prec, level in TOL.items():
-            xr, vr, ex, ev = trajectory_envelope(*args, eps, h, 16, level)
+        for prec, tq in TOLQ.items():
+            xr, vr, ex, ev = trajectory_envelope(*args, eps, h, 16, tq[:3])
             env[prec] = (ex, ev)
         refs.append((start, xr, vr, env))
     return batch, eps, h, refs
 
 
-@pytest.mark.parametrize("precision", ["fp64", "ex"])
+@pytest.mark.parametrize("precision", ["fp64", "ex", "fp32x"])
 def test_uneven_batch_shared_steps_vs_oracle(nb, shared_reference, precision):
     """Start-up a, jerk, snap, potential at the evaluation bound; after 16
     shared steps every particle within 2e-14 + 4 x the oracle's own
@@ -112,14 +116,14 @@ def test_uneven_batch_shared_steps_vs_oracle(nb, shared_reference, precision):
     sim = nb.Simulation(batch.m, batch.x, batch.v, eps=eps, precision=precision,
                         offsets=batch.offsets, dt_min=h, dt_max=h)
     st0 = sim.state_numpy()
-    tol = TOL[precision]
+    tq = TOLQ[precision]
     for c, (start, _, _, _) in enumerate(refs):
         lo, hi = batch.offsets[c], batch.offsets[c + 1]
-        for f in ("a", "j", "s"):
+        for f, tol in zip(("a", "j", "s"), tq):
             e = rel_rows(st0[f][lo:hi], start[f])
             assert e.max() <= tol, f"cluster {c} (n={hi - lo}) start-up {f}: {e.max():.3e}"
         e = rel_pot(st0["pot"][lo:hi], start["pot"])
-        assert e.max() <= tol, f"cluster {c} start-up pot: {e.max():.3e}"
+        assert e.max() <= tq[3], f"cluster {c} start-up pot: {e.max():.3e}"
     steps, inter = sim.run(16 * h)
     assert steps == 16 * len(SHARED_SIZES)
     n_tot = float(sum(k * (k - 1) for k in SHARED_SIZES))
@@ -144,14 +148,20 @@ def test_uneven_batch_shared_steps_vs_oracle(nb, shared_reference, precision):
 
 
 # ----------------------------------------- block steps, identical states
-@pytest.mark.parametrize("precision", ["fp64", "ex"])
+@pytest.mark.parametrize("precision", ["fp64", "ex", "fp32x"])
 def test_block_steps_match_oracle_step_by_step(nb, oracle, precision):
     eps = 1e-4
     batch = ic.plummer_batch(sizes=BLOCK_SIZES, seed=32)
     sim = nb.Simulation(batch.m, batch.x, batch.v, eps=eps, precision=precision,
                         offsets=batch.offsets)
-    tol = TOL[precision]
-    xtol, vtol = (1e-14, 1e-13) if precision == "fp64" else (1e-12, 1e-11)
+    tq = TOLQ[precision]
+    # positions and velocities of one corrected step: rounding (FP64), the
+    # float-float evaluation (EX); with FP32X the corrector carries FP32 jerk
+    # and snap errors through its h^2/10 and h^3/120 terms
+    xtol, vtol = {"fp64": (1e-14, 1e-13), "ex": (1e-12, 1e-11), "fp32x": (1e-10, 1e-9)}[precision]
+    # FP32X's jerk and snap (2e-5) enter the criterion's interpolated
+    # derivatives: a step landing near a power of two flips more often
+    dt_flips = 500 if precision != "fp32x" else 50
     n_active_seen = []
     for step in range(8):
         pre = sim.state_numpy()
@@ -172,15 +182,15 @@ def test_block_steps_match_oracle_step_by_step(nb, oracle, precision):
             for f, tl in (("x", xtol), ("v", vtol)):
                 e = rel_rows(post[f][lo:hi][act], getattr(ref, f)[act])
                 assert e.max(initial=0.0) <= tl, f"step {step} cluster {c} {f}: {e.max():.3e}"
-            for f in ("a", "j", "s"):
+            for f, tol in zip(("a", "j", "s"), tq):
                 e = rel_rows(post[f][lo:hi][act], getattr(ref, f)[act])
                 assert e.max(initial=0.0) <= tol, f"step {step} cluster {c} {f}: {e.max():.3e}"
             e = rel_pot(post["pot"][lo:hi][act], ref.pot[act])
-            assert e.max(initial=0.0) <= tol, f"step {step} cluster {c} pot: {e.max():.3e}"
+            assert e.max(initial=0.0) <= tq[3], f"step {step} cluster {c} pot: {e.max():.3e}"
             # new steps: a criterion landing within rounding of a power of two
             # may quantise either way (rare)
             mism = np.count_nonzero(post["dt"][lo:hi][act] != ref.dt[act])
-            assert mism <= max(1, len(act) // 500), (step, c, mism)
+            assert mism <= max(1, len(act) // dt_flips), (step, c, mism)
             # untouched particles stay bit-identical
             idle = np.setdiff1d(np.arange(hi - lo), act)
             for f in ("x", "v", "a", "t", "dt"):
