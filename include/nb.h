@@ -302,8 +302,7 @@ nb_status nb_autotune(nb_ctx *ctx, const char *cache_path);
  *   stream   : cudaStream_t (NULL = legacy default); the call synchronises it
  *              to read its error word
  * The first call on a device looks up the array's device address with that
- * device current (make that first call before any stream capture).  Every
- * call copies its error word to the host and synchronises `stream` before
+ * device current.  Every call copies its error word to the host and synchronises `stream` before
  * it returns.  All calls share the array: calls that overlap on the GPU
  * (other streams, threads or processes sharing the library) race and must
  * be serialised by the caller.  Errors: NB_EINVAL (sizes, NULL pointers, an

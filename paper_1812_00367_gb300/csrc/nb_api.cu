@@ -54,7 +54,8 @@ struct nb_ctx {
     cudaStream_t stream = nullptr;      // caller's stream (launches, graph replays)
     cudaStream_t cap_stream = nullptr;  // private stream used only for capture
     cudaStream_t cap_side = nullptr;    // second capture branch (predictor)
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t cap_side2 = nullptr;   // third capture branch (planner)
+    cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
     nb_params p{};
     int64_t n = 0;
     int32_t nc = 1;
@@ -160,15 +161,18 @@ constexpr int kKernelsPerStep = 5;
 cudaError_t enqueue_step(nb_ctx *ctx, cudaStream_t st, int slot) {
     cudaError_t e;
     if ((e = launch_select_min(ctx->d, st)) != cudaSuccess) return e;
-    if ((e = launch_select_compact(ctx->d, 0.0, st)) != cudaSuccess) return e;
-    // the planner and the predictor both need only the selection: two graph
-    // branches, joined before the evaluation
+    // the compaction, the planner and the predictor all need only pass 1's
+    // t_next and counts: three graph branches, joined before the evaluation
     if ((e = cudaEventRecord(ctx->fork, st)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(ctx->cap_side, ctx->fork, 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ctx->cap_side2, ctx->fork, 0)) != cudaSuccess) return e;
     if ((e = launch_predict(ctx->d, 0, 0, 0.0, ctx->cap_side)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(ctx->join, ctx->cap_side)) != cudaSuccess) return e;
-    if ((e = launch_plan_ex(ctx->d, 0, 1, st)) != cudaSuccess) return e;
+    if ((e = launch_plan_ex(ctx->d, 0, 1, ctx->cap_side2)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ctx->join2, ctx->cap_side2)) != cudaSuccess) return e;
+    if ((e = launch_select_compact(ctx->d, 0.0, st)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(st, ctx->join, 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, ctx->join2, 0)) != cudaSuccess) return e;
     EvalLaunch L{};
     if (slot >= 0 && (e = cudaEventRecordWithFlags(ctx->ev[2 * slot], st, cudaEventRecordExternal)) != cudaSuccess)
         return e;
@@ -319,6 +323,8 @@ void nb_free(nb_ctx *ctx) {
     for (cudaEvent_t ev : ctx->ev) cudaEventDestroy(ev);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->cap_side) cudaStreamDestroy(ctx->cap_side);
+    if (ctx->cap_side2) cudaStreamDestroy(ctx->cap_side2);
+    if (ctx->join2) cudaEventDestroy(ctx->join2);
     if (ctx->fork) cudaEventDestroy(ctx->fork);
     if (ctx->join) cudaEventDestroy(ctx->join);
     delete ctx;
@@ -365,6 +371,8 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_side2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join2, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_busy, sizeof(int32_t));
@@ -462,6 +470,7 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     ALLOC(d.plan, n_clusters);
     ALLOC(d.n_items, 1);
     ALLOC(d.item_ctr, 1);
+    ALLOC(d.sel_ctr, 1);
     ALLOC(ctx->d_table, kBuckets);
     ALLOC(d.partial, ctx->cap_items * 10 * kTPB);
     const int64_t max_tiles = n + n_clusters + 1;
@@ -516,6 +525,7 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     if (ok && cudaMemsetAsync(d.ctr_underflow, 0, sizeof(unsigned long long), s0) != cudaSuccess) ok = false;
     if (ok && cudaMemsetAsync(d.err, 0, sizeof(uint32_t), s0) != cudaSuccess) ok = false;
     if (ok && cudaMemsetAsync(d.busy, 0, sizeof(int32_t), s0) != cudaSuccess) ok = false;
+    if (ok && cudaMemsetAsync(d.sel_ctr, 0, sizeof(unsigned int), s0) != cudaSuccess) ok = false;
     // the chunk tables live in pageable host vectors: finish the copies here
     if (ok && cudaStreamSynchronize(s0) != cudaSuccess) ok = false;
     if (!ok) {

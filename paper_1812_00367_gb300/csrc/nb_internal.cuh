@@ -214,6 +214,7 @@ struct Dev {
     // it among the fields above measured 2.8 % slower FP64 evaluation.
     int32_t order;
     int32_t streamk_off;  // NB_NO_STREAMK
+    unsigned int *sel_ctr;  // [1]: chunks done in select pass 1 (the last one finishes the pass)
 };
 
 // How one evaluation launch obtains its work.

@@ -5,10 +5,13 @@
 // t_next = min_i (t_i + dt_i) per cluster, active = {i : t_i + dt_i == t_next}
 // in increasing index order.  Two passes over fixed chunks of kChunk
 // particles (chunks never straddle clusters): pass 1 writes each chunk's
-// minimum and how many of its particles reach it; pass 2 combines the chunk
-// minima of the cluster, computes the chunk's offset from the counts of the
-// earlier chunks and compacts its active particles in order.  No atomics, so
-// the active list is deterministic.
+// minimum and how many of its particles reach it, and its last CTA (a
+// counter) combines the chunk minima and counts of every cluster into the
+// cluster's t_next and active count; pass 2 computes each chunk's offset from
+// the counts of the cluster's earlier chunks and compacts its active
+// particles in order.  The planner and the predictor need only t_next and the
+// count, so they run beside pass 2.  The active list takes no atomics and is
+// deterministic.
 #include "nb_internal.cuh"
 #include "nb_step.cuh"
 
@@ -48,39 +51,107 @@ __global__ void __launch_bounds__(kSelTPB) k_select_min(const Dev d) {
     int cnt = 0;
     for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) cnt += (d.t[i] + d.dt[i] == mn);
     cnt = block_reduce(cnt, SumI(), smi);
+    __shared__ int last;
     if (threadIdx.x == 0) {
         d.chunk_min[k] = mn;
         d.chunk_cnt[k] = cnt;
+        __threadfence();
+        last = atomicAdd(d.sel_ctr, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last) return;
+    // The last CTA: each cluster's t_next = the least chunk minimum, its
+    // active count = the counts of the chunks that reach it.  A cluster of at
+    // most kSelThread chunks is taken by one thread, one of at most kSelWarp
+    // chunks by a warp (its lanes load the chunk values side by side), larger
+    // ones by the whole CTA; clusters that find their list full fall back to
+    // the tier below.
+    __threadfence();
+    constexpr int kSelThread = 8;
+    constexpr int kSelWarp = 64;
+    constexpr int kSelMid = 256;
+    constexpr int kSelLarge = 64;
+    __shared__ int mid[kSelMid];
+    __shared__ int large[kSelLarge];
+    __shared__ int n_mid, n_large;
+    if (threadIdx.x == 0) n_mid = n_large = 0;
+    __syncthreads();
+    const double t_end = *d.t_end;
+    for (int c = threadIdx.x; c < d.n_clusters; c += blockDim.x) {
+        const int k0 = d.cluster_chunk0[c], k1 = d.cluster_chunk0[c + 1];
+        if (k1 - k0 > kSelWarp) {
+            const int slot = atomicAdd(&n_large, 1);
+            if (slot < kSelLarge) {
+                large[slot] = c;
+                continue;
+            }
+        }
+        if (k1 - k0 > kSelThread) {
+            const int slot = atomicAdd(&n_mid, 1);
+            if (slot < kSelMid) {
+                mid[slot] = c;
+                continue;
+            }
+        }
+        double tn = INFINITY;
+        for (int kk = k0; kk < k1; ++kk) tn = fmin(tn, __ldcg(&d.chunk_min[kk]));
+        int total = 0;
+        for (int kk = k0; kk < k1; ++kk)
+            if (__ldcg(&d.chunk_min[kk]) == tn) total += __ldcg(&d.chunk_cnt[kk]);
+        d.tnext[c] = tn;
+        d.nact[c] = tn <= t_end ? total : 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int nm = n_mid < kSelMid ? n_mid : kSelMid;
+    for (int q = threadIdx.x >> 5; q < nm; q += nwarps) {
+        const int c = mid[q];
+        const int k0 = d.cluster_chunk0[c], k1 = d.cluster_chunk0[c + 1];
+        double tn = INFINITY;
+        for (int kk = k0 + lane; kk < k1; kk += 32) tn = fmin(tn, __ldcg(&d.chunk_min[kk]));
+        for (int o = 16; o >= 1; o >>= 1) tn = fmin(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+        int total = 0;
+        for (int kk = k0 + lane; kk < k1; kk += 32)
+            if (__ldcg(&d.chunk_min[kk]) == tn) total += __ldcg(&d.chunk_cnt[kk]);
+        for (int o = 16; o >= 1; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        if (lane == 0) {
+            d.tnext[c] = tn;
+            d.nact[c] = tn <= t_end ? total : 0;
+        }
+    }
+    const int nl = n_large < kSelLarge ? n_large : kSelLarge;
+    for (int q = 0; q < nl; ++q) {
+        const int c = large[q];
+        const int k0 = d.cluster_chunk0[c], k1 = d.cluster_chunk0[c + 1];
+        double tn = INFINITY;
+        for (int kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) tn = fmin(tn, __ldcg(&d.chunk_min[kk]));
+        tn = block_reduce(tn, MinOp(), smd);
+        int total = 0;
+        for (int kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x)
+            if (__ldcg(&d.chunk_min[kk]) == tn) total += __ldcg(&d.chunk_cnt[kk]);
+        total = block_reduce(total, SumI(), smi);
+        if (threadIdx.x == 0) {
+            d.tnext[c] = tn;
+            d.nact[c] = tn <= t_end ? total : 0;
+        }
+    }
+    if (threadIdx.x == 0) *d.sel_ctr = 0u;  // ready for the next pass
 }
 
 // -------------------------------------------------------------- select pass 2
 __global__ void __launch_bounds__(kSelTPB) k_select_compact(const Dev d) {
-    __shared__ double smd[kSelTPB / 32];
     __shared__ int smi[kSelTPB / 32];
     __shared__ int warp_cnt[kSelTPB / 32];
     const int k = blockIdx.x;
     const int c = d.chunk_cluster[k];
-    const int k0 = d.cluster_chunk0[c], k1 = d.cluster_chunk0[c + 1];
-    double tn = INFINITY;
-    for (int kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) tn = fmin(tn, d.chunk_min[kk]);
-    tn = block_reduce(tn, MinOp(), smd);
-    int before = 0, total = 0;
-    for (int kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
-        if (d.chunk_min[kk] == tn) {
-            const int cn = d.chunk_cnt[kk];
-            total += cn;
-            if (kk < k) before += cn;
-        }
-    }
+    const int k0 = d.cluster_chunk0[c];
+    // t_next and the count come from pass 1's last CTA
+    const double tn = d.tnext[c];
+    if (d.nact[c] == 0 || d.chunk_min[k] != tn) return;
+    int before = 0;
+    for (int kk = k0 + threadIdx.x; kk < k; kk += blockDim.x)
+        if (d.chunk_min[kk] == tn) before += d.chunk_cnt[kk];
     before = block_reduce(before, SumI(), smi);
-    total = block_reduce(total, SumI(), smi);
-    const bool go = tn <= *d.t_end;
-    if (k == k0 && threadIdx.x == 0) {
-        d.tnext[c] = tn;
-        d.nact[c] = go ? total : 0;
-    }
-    if (!go || d.chunk_min[k] != tn) return;
     const int64_t b = d.chunk_begin[k], e = d.chunk_end[k];
     int32_t *out = d.active + d.offsets[c] + before;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

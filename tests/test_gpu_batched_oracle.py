@@ -239,3 +239,49 @@ def test_512_cluster_batch_startup_and_selection(nb, oracle, precision):
                 assert e.max(initial=0.0) <= TOL[precision], (c, f, e.max())
     assert na_sum == na_tot
     sim.close()
+
+
+# ------------------------------- clusters larger than 32 selection chunks
+@pytest.mark.parametrize("sizes", [[140000], [300, 70000, 1000, 2], [20000, 140000]])
+def test_selection_of_large_clusters(nb, oracle, sizes):
+    """The last CTA of the first selection pass combines the chunk minima
+    and counts (chunks of 2048 particles) of a cluster of at most 8 chunks in
+    one thread, of at most 64 chunks in one warp, of more in the whole CTA:
+    140000 particles (69 chunks), 70000 (35), 20000 (10) and the small
+    clusters cover the three tiers.  Over six block steps every
+    cluster's (t_next, active set) is the oracle scheduler's on the same
+    state, and the a, jerk, snap and potential the step stores are the
+    oracle's sums on the same predicted state (the GPU predictor's output:
+    with a close pair at eps 1e-4, the two predictors' roundings alone move
+    the jerk by more than 1e-12)."""
+    eps = 1e-4
+    batch = ic.plummer_batch(sizes=sizes, seed=33)
+    sim = nb.Simulation(batch.m, batch.x, batch.v, eps=eps, precision="fp64",
+                        offsets=None if len(sizes) == 1 else batch.offsets)
+    for step in range(6):
+        pre = sim.state_numpy()
+        plan = []
+        for c in range(len(sizes)):
+            lo, hi = batch.offsets[c], batch.offsets[c + 1]
+            tn_c, act = oracle_on_state(oracle, pre, lo, hi, eps).select()
+            pred = sim.predict(tn_c).cpu().numpy()[:, lo:hi] if len(act) else None
+            plan.append((tn_c, act, pred))
+        tn_min, na_tot = sim.step()
+        post = sim.state_numpy()
+        na_sum = 0
+        for c, (tn_c, act, pred) in enumerate(plan):
+            lo, hi = batch.offsets[c], batch.offsets[c + 1]
+            moved = np.nonzero(post["t"][lo:hi] != pre["t"][lo:hi])[0]
+            np.testing.assert_array_equal(moved, act, err_msg=f"step {step} cluster {c}")
+            assert np.all(post["t"][lo:hi][act] == tn_c)
+            na_sum += len(act)
+            if not len(act):
+                continue
+            acc, jrk, snp, pot = oracle.force(batch.m[lo:hi], pred[0:3].T, pred[3:6].T,
+                                              pred[6:9].T, eps, active=act)
+            for f, r in (("a", acc), ("j", jrk), ("s", snp)):
+                e = rel_rows(post[f][lo:hi][act], r)
+                assert e.max(initial=0.0) <= 1e-12, (step, c, f, e.max())
+            assert rel_pot(post["pot"][lo:hi][act], pot).max(initial=0.0) <= 1e-12
+        assert na_tot == na_sum
+    sim.close()
