@@ -411,7 +411,7 @@ nb_status nb_init(nb_ctx **out, const nb_params *p, int64_t n, const nb_state *s
     d.streamk_off = (p->flags & NB_NO_STREAMK) ? 1 : 0;
     d.m = st->m; d.x = st->x; d.v = st->v; d.a = st->a; d.j = st->j; d.s = st->s; d.c = st->c;
     d.t = st->t; d.dt = st->dt; d.pot = st->pot;
-    d.eps2 = p->eps * p->eps;
+    set_eps2(d, p->eps);
     d.eta = p->eta;
     d.eta_init = p->eta_init;
     d.dt_min = p->dt_min;

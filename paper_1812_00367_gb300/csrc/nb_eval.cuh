@@ -851,10 +851,8 @@ __global__ void __launch_bounds__(kTPB, (eval_min_blocks<P, MODE>())) k_eval(con
         for (int q = 0; q < 10; ++q) t64[q * t64st] = 0.0;
         const double eps2 = d.eps2;
         const float eps2f = (float)eps2;
-        const float2 eps2f2 = make_float2(eps2f, eps2f);
-        ff2 eps2ff2;
-        eps2ff2.hi = f2s((float)eps2);
-        eps2ff2.lo = f2s((float)(eps2 - (double)(float)eps2));
+        const float2 eps2f2 = d.eps2_hi2;
+        const ff2 eps2ff2{d.eps2_hi2, d.eps2_lo2};
 
         const bool warp_active = __any_sync(0xffffffffu, valid);
 

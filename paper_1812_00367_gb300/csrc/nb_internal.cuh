@@ -215,7 +215,21 @@ struct Dev {
     int32_t order;
     int32_t streamk_off;  // NB_NO_STREAMK
     unsigned int *sel_ctr;  // [1]: chunks done in select pass 1 (the last one finishes the pass)
+    // eps^2 as a float-float pair, both lanes equal: hi = fl(eps^2),
+    // lo = fl(eps^2 - hi).  Formed on the host: the single-precision kernels
+    // read them as parameters, where converting eps2 in the kernel costs
+    // FP64-pipe conversions wherever the compiler re-forms the values.
+    float2 eps2_hi2, eps2_lo2;
 };
+
+// eps^2 and its float-float pair (host side; every context and launch).
+inline void set_eps2(Dev &d, double eps) {
+    d.eps2 = eps * eps;
+    const float hi = (float)d.eps2;
+    const float lo = (float)(d.eps2 - (double)hi);
+    d.eps2_hi2 = make_float2(hi, hi);
+    d.eps2_lo2 = make_float2(lo, lo);
+}
 
 // How one evaluation launch obtains its work.
 struct EvalLaunch {

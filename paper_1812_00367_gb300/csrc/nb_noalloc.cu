@@ -175,7 +175,7 @@ extern "C" nb_status nb_evaluate_noalloc(const double *jpred, int64_t n, double 
     d.partial_cap = kNaMaxItems * 10 * kTPB;  // doubles
     d.tile_cnt = reinterpret_cast<int32_t *>(slot.base + kNaOffTile);
     d.err = &aux->err;
-    d.eps2 = eps * eps;
+    set_eps2(d, eps);
     d.neg_one = -1.0;
     d.neg_zero = -0.0;
     EvalLaunch L{};
