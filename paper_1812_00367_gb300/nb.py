@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
             "nb_probe_fma_peak": ([i32, i64, vp, pd, pd], C.c_int),
             "nb_selftest_wait_timeout": ([d, vp], C.c_int),
             "nb_probe_rsqrt": ([i32, vp, vp, i64, vp], C.c_int),
+            "nb_evaluate_noalloc": ([vp, i64, d, vp, i32, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
