@@ -4,8 +4,8 @@
  *
  * The paper (Goz et al., "Astrophysical code migration into Exascale Era")
  * states the problem this library computes:
- *   - Sec. 2: a direct N-body code that "relies on the Hermite 6th order time
- *     integrator", derived from HiGPUs; double precision is needed for the
+ *   - Sec. 2: a direct N-body code built on a 6th-order Hermite integrator
+ *     and descended from HiGPUs; double precision is needed for the
  *     inter-particle distance and the acceleration; an extended-precision
  *     ("EX") number type built from pairs of single-precision numbers is the
  *     alternative on devices with weak double precision.

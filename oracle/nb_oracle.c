@@ -9,10 +9,10 @@
  * generator (paper_1812_00367_gb300/ic.py), which holds none of the method.
  *
  * What the paper fixes and what comes from the method it builds on:
- *   - Sec. 2: the code "relies on the Hermite 6th order time integrator" and is
- *     derived from HiGPUs; distance and acceleration need double precision.
+ *   - Sec. 2: the code integrates with a 6th-order Hermite scheme and descends
+ *     from HiGPUs; distance and acceleration need double precision.
  *   - Sec. 4: the O(N^2) kernel (acceleration, jerk, snap of every active
- *     particle against all others) is the most computationally demanding step.
+ *     particle against all others) is where the run spends its time.
  *   - The paper prints no formulas.  The evaluation, predictor, corrector,
  *     quintic interpolation and time-step criterion below follow the published
  *     6th-order Hermite scheme of Nitadori & Makino 2008 (New Astron. 13, 498;
