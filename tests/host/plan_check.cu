@@ -1,8 +1,10 @@
 // plan_check.cu -- host-only checks of the work-planning arithmetic shared by
-// the evaluation kernel and its planners (stream-K ranges, split choice).
+// the evaluation kernel and its planners (stream-K ranges, split choice), and
+// of the host-formed launch parameters (eps^2 as a float-float pair).
 // Runs on the CPU: it makes no CUDA call.  Prints "ok <cases>" or the first
 // violated property and exits non-zero.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -110,8 +112,34 @@ static void check_split(int64_t tiles, int64_t ntj, int64_t target, int64_t grid
     }
 }
 
+// eps^2 as the single-precision kernels read it: hi = fl32(eps^2), lo the
+// float nearest the remainder, both lanes equal; the pair holds eps^2 to
+// within half an ulp of lo (about 2^-48 relative) and is normalised.
+static void check_eps2(double eps) {
+    Dev d{};
+    set_eps2(d, eps);
+    const double e2 = eps * eps;
+    CHECK(d.eps2 == e2, "eps %.17g", eps);
+    CHECK(d.eps2_hi2.x == (float)e2 && d.eps2_hi2.y == d.eps2_hi2.x, "hi of eps %.17g", eps);
+    CHECK(d.eps2_lo2.y == d.eps2_lo2.x, "lo lanes of eps %.17g", eps);
+    const double hi = d.eps2_hi2.x, lo = d.eps2_lo2.x;
+    CHECK(std::fabs(lo) <= 0.5 * std::ldexp(1.0, std::ilogb(hi > 0 ? hi : 1.0) - 23) || hi == 0.0,
+          "lo not below half an ulp of hi, eps %.17g", eps);
+    CHECK(std::fabs(hi + lo - e2) <= std::ldexp(std::fabs(e2), -47), "pair error, eps %.17g: %.3g", eps,
+          std::fabs(hi + lo - e2) / e2);
+}
+
 int main() {
     int cases = 0;
+    for (double eps : {0.0, 1e-5, 1e-4, 1e-3, 1e-2, 0.1, 1.0}) {
+        check_eps2(eps);
+        ++cases;
+    }
+    // eps^2 in [2^-100, 2^100], where lo (about 2^-24 eps^2) is a normal float
+    for (int r = 0; r < 2000; ++r) {
+        check_eps2(std::exp2(-50.0 + 100.0 * (double)(next_u64() >> 11) * 0x1.0p-53));
+        ++cases;
+    }
     const int64_t grids[] = {152, 456, 608, 1216};
     // fixed shapes of the benchmark system, then random ones
     const int64_t fixed[][2] = {{512, 1024}, {299, 1024}, {67, 1024}, {3, 1024}, {16, 257}, {1000, 3}};
